@@ -1,0 +1,220 @@
+"""Test-side helpers: hand-built meshes, golden fixtures, brute-force definitions
+and invariant checks.  Independent of both the oracle and the CUDA library.
+
+The brute force here restates the paper's definitions in the most direct form
+(Section 3.2.1, Algorithm 2; terminal-edge regions as connected components), with
+Python integers and union-find, so that the oracle's walk-based code is checked
+against something other than itself.
+"""
+from __future__ import annotations
+
+import glob
+import json
+import os
+
+import numpy as np
+
+import meshgen
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_cases():
+    out = []
+    for path in sorted(glob.glob(os.path.join(GOLDEN, "*.json"))):
+        with open(path) as f:
+            case = json.load(f)
+        case["name"] = os.path.splitext(os.path.basename(path))[0]
+        tri = np.asarray(case["tri"], dtype=np.int32)
+        case["mesh"] = {"xy": np.asarray(case["xy"], dtype=np.int64), "tri": tri,
+                        "twin": meshgen.twin_from_tri(tri)}
+        out.append(case)
+    return out
+
+
+def grid_mesh(k: int, seed: int = 0, step: int = 1):
+    """k x k unit cells, one diagonal per cell in a random direction.
+
+    Closed form (each cell's diagonal is the longest edge of both of its
+    triangles, every side is the longest edge of neither): k^2 square polygons,
+    cell c's seed is its first triangle 2c, the polygon is the cell's four corners
+    ccw from the smallest vertex id, and nothing is repaired."""
+    rng = np.random.default_rng(seed)
+    vid = lambda i, j: j * (k + 1) + i  # noqa: E731
+    xy = np.array([(i * step, j * step) for j in range(k + 1) for i in range(k + 1)], np.int64)
+    tri, polys = [], []
+    for j in range(k):
+        for i in range(k):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            if rng.integers(2):
+                tri += [(a, b, c), (a, c, d)]
+            else:
+                tri += [(a, b, d), (b, c, d)]
+            polys.append([a, b, c, d])  # ccw, a is the smallest id
+    tri = np.asarray(tri, np.int32)
+    return {"xy": xy, "tri": tri, "twin": meshgen.twin_from_tri(tri)}, polys
+
+
+def csr_to_lists(off, vtx):
+    off = np.asarray(off)
+    vtx = np.asarray(vtx)
+    return [vtx[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+
+
+# ------------------------------------------------------------------ brute force
+def brute_labels(mesh):
+    """Longest edge, terminal, frontier and seed flags straight from the definitions."""
+    xy = [tuple(map(int, p)) for p in mesh["xy"]]
+    tri = [tuple(map(int, t)) for t in mesh["tri"]]
+    twin = [int(g) for g in mesh["twin"]]
+    m = len(tri)
+
+    def ends(h):
+        t, k = divmod(h, 3)
+        return tri[t][k], tri[t][(k + 1) % 3]
+
+    def key(h):  # larger key = longer edge
+        a, b = ends(h)
+        d2 = (xy[a][0] - xy[b][0]) ** 2 + (xy[a][1] - xy[b][1]) ** 2
+        eid = h if twin[h] < 0 else min(h, twin[h])
+        return (d2, -eid)
+
+    max_edge = [max(range(3), key=lambda k, t=t: key(3 * t + k)) for t in range(m)]
+    is_max = [max_edge[h // 3] == h % 3 for h in range(3 * m)]
+    terminal = [0] * (3 * m)
+    frontier = [0] * (3 * m)
+    seed = [0] * m
+    for h in range(3 * m):
+        g = twin[h]
+        if g < 0:
+            frontier[h] = 1
+            if is_max[h]:
+                terminal[h] = 1
+                seed[h // 3] = 1
+        else:
+            if is_max[h] and is_max[g]:
+                terminal[h] = 1
+                seed[min(h // 3, g // 3)] = 1
+            if not is_max[h] and not is_max[g]:
+                frontier[h] = 1
+    return {"max_edge": max_edge, "terminal": terminal, "frontier": frontier, "seed": seed}
+
+
+def brute_regions(mesh, frontier):
+    """Union-find components of triangles joined across non-frontier edges, and for
+    each component the multiset of its frontier half-edges as (origin, dest)."""
+    tri = [tuple(map(int, t)) for t in mesh["tri"]]
+    twin = [int(g) for g in mesh["twin"]]
+    m = len(tri)
+    parent = list(range(m))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for h in range(3 * m):
+        g = twin[h]
+        if g >= 0 and not frontier[h]:
+            ra, rb = find(h // 3), find(g // 3)
+            if ra != rb:
+                parent[ra] = rb
+    comp = [find(t) for t in range(m)]
+    bnd = {}
+    for h in range(3 * m):
+        if frontier[h]:
+            t, k = divmod(h, 3)
+            bnd.setdefault(comp[t], []).append((tri[t][k], tri[t][(k + 1) % 3]))
+    return comp, {c: sorted(v) for c, v in bnd.items()}
+
+
+def lepp_end(mesh, max_edge):
+    """Follow each triangle's longest-edge link until a terminal edge: returns the
+    terminal edge (as a sorted vertex pair) reached from every triangle."""
+    tri = [tuple(map(int, t)) for t in mesh["tri"]]
+    twin = [int(g) for g in mesh["twin"]]
+    m = len(tri)
+    out = []
+    for t in range(m):
+        cur, steps = t, 0
+        while True:
+            h = 3 * cur + max_edge[cur]
+            g = twin[h]
+            if g < 0 or max_edge[g // 3] == g % 3:
+                k = max_edge[cur]
+                out.append(tuple(sorted((tri[cur][k], tri[cur][(k + 1) % 3]))))
+                break
+            cur = g // 3
+            steps += 1
+            assert steps <= m, "longest-edge links form a cycle"
+    return out
+
+
+# ------------------------------------------------------------------ invariants
+def twice_area(poly, xy):
+    s = 0
+    n = len(poly)
+    for i in range(n):
+        a, b = xy[poly[i]], xy[poly[(i + 1) % n]]
+        s += int(a[0]) * int(b[1]) - int(b[0]) * int(a[1])
+    return s
+
+
+def hull_twice_area(xy):
+    pts = sorted(set((int(p[0]), int(p[1])) for p in xy))
+
+    def cross(o, a, b):
+        return (a[0] - o[0]) * (b[1] - o[1]) - (a[1] - o[1]) * (b[0] - o[0])
+
+    lower, upper = [], []
+    for p in pts:
+        while len(lower) >= 2 and cross(lower[-2], lower[-1], p) <= 0:
+            lower.pop()
+        lower.append(p)
+    for p in reversed(pts):
+        while len(upper) >= 2 and cross(upper[-2], upper[-1], p) <= 0:
+            upper.pop()
+        upper.append(p)
+    hull = lower[:-1] + upper[:-1]
+    s = 0
+    for i in range(len(hull)):
+        a, b = hull[i], hull[(i + 1) % len(hull)]
+        s += a[0] * b[1] - b[0] * a[1]
+    return s
+
+
+def tips(poly):
+    n = len(poly)
+    return [poly[(i + 1) % n] for i in range(n) if poly[i] == poly[(i + 2) % n]]
+
+
+def check_final_mesh(mesh, polys, frontier_final):
+    """Invariants of the final polygonal mesh (Section 3.2.3's output): every
+    polygon simple, ccw, with positive area; areas add up to the domain (hull)
+    area; the polygons' edges are exactly the frontier edges (each frontier
+    half-edge in exactly one polygon); every vertex is used; Euler V - E + F = 1."""
+    xy = mesh["xy"]
+    tri = mesh["tri"]
+    n = xy.shape[0]
+    tot = 0
+    used = set()
+    directed = []
+    for p in polys:
+        assert len(p) >= 3
+        assert len(set(p)) == len(p), f"polygon not simple: {p}"
+        a = twice_area(p, xy)
+        assert a > 0, f"polygon not ccw / zero area: {p}"
+        tot += a
+        used.update(p)
+        directed += [(p[i], p[(i + 1) % len(p)]) for i in range(len(p))]
+    assert tot == hull_twice_area(xy), "areas do not sum to the domain area"
+    assert used == set(range(n)), "vertex set changed"
+    assert len(directed) == len(set(directed)), "a half-edge is in two polygons"
+    org = tri.reshape(-1)
+    dst = tri[:, [1, 2, 0]].reshape(-1)
+    fr = np.asarray(frontier_final).astype(bool)
+    expect = sorted(zip(org[fr].tolist(), dst[fr].tolist()))
+    assert sorted(directed) == expect, "polygon edges differ from the frontier half-edges"
+    undirected = {tuple(sorted(e)) for e in directed}
+    assert n - len(undirected) + len(polys) == 1, "Euler characteristic"

@@ -1,0 +1,216 @@
+"""Pins for the CPU oracle: hand-built cases with expected values written by hand
+from the paper's definitions (tests/golden), the k x k grid closed form, brute
+force on tiny Delaunay meshes, invariants on larger ones, and planted mistakes
+that the pins must catch.  No GPU."""
+from __future__ import annotations
+
+import os
+import shutil
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from meshlib import (brute_labels, brute_regions, check_final_mesh, csr_to_lists, golden_cases,
+                     grid_mesh, lepp_end, tips)
+
+GOLDEN = golden_cases()
+
+
+def _halfedges(flags):
+    return np.nonzero(np.asarray(flags))[0].tolist()
+
+
+# --------------------------------------------------------------------- pin suite
+def pin_golden(case, lib=None):
+    e = case["expect"]
+    r = oracle.full(case["mesh"], lib)
+    lab = r["label"]
+    assert lab["max_edge"].tolist() == e["max_edge"]
+    assert _halfedges(lab["terminal"]) == e["terminal_halfedges"]
+    assert _halfedges(lab["frontier"]) == e["frontier_halfedges"]
+    assert r["seeds"].tolist() == e["seeds"]
+    assert csr_to_lists(r["trav_off"], r["trav_vtx"]) == e["traverse"]
+    assert csr_to_lists(r["off"], r["vtx"]) == e["final"]
+    assert r["splits"] == e["splits"]
+    added = sorted(set(_halfedges(r["frontier_final"])) - set(e["frontier_halfedges"]))
+    assert added == e.get("final_new_frontier_halfedges", [])
+
+
+def pin_grid(k, seed, lib=None):
+    mesh, polys = grid_mesh(k, seed)
+    r = oracle.full(mesh, lib)
+    m = 2 * k * k
+    assert r["seeds"].tolist() == list(range(0, m, 2))
+    assert csr_to_lists(r["trav_off"], r["trav_vtx"]) == polys
+    assert csr_to_lists(r["off"], r["vtx"]) == polys
+    assert r["splits"] == 0
+    # the diagonal (local edge 2 of the first and 0 / 1 of the second triangle) is
+    # the only non-frontier edge of every cell
+    fr = r["label"]["frontier"].reshape(m, 3)
+    assert int(fr.sum()) == 3 * m - 2 * k * k
+
+
+def pin_bruteforce(mesh, lib=None):
+    r = oracle.full(mesh, lib)
+    b = brute_labels(mesh)
+    lab = r["label"]
+    assert lab["max_edge"].tolist() == b["max_edge"]
+    assert lab["terminal"].tolist() == b["terminal"]
+    assert lab["frontier"].tolist() == b["frontier"]
+    assert lab["seed"].tolist() == b["seed"]
+    comp, bnd = brute_regions(mesh, b["frontier"])
+    seeds = r["seeds"].tolist()
+    # one seed per region, and every region has one
+    assert sorted(comp[s] for s in seeds) == sorted(set(comp))
+    # each region's longest-edge paths all end at the same terminal edge
+    ends = lepp_end(mesh, b["max_edge"])
+    for c in set(comp):
+        assert len({ends[t] for t in range(len(comp)) if comp[t] == c}) == 1
+    polys = csr_to_lists(r["trav_off"], r["trav_vtx"])
+    assert len(polys) == len(seeds)
+    for s, p in zip(seeds, polys):
+        edges = sorted((p[i], p[(i + 1) % len(p)]) for i in range(len(p)))
+        assert edges == bnd[comp[s]], "polygon is not the region boundary"
+        assert p[0] == min(p), "polygon does not start at its smallest vertex"
+    final = csr_to_lists(r["off"], r["vtx"])
+    check_final_mesh(mesh, final, r["frontier_final"])
+    assert len(final) == len(polys) + r["splits"]
+    assert len(r["vtx"]) == len(r["trav_vtx"]) + 2 * r["splits"]
+    return r
+
+
+def tiny_meshes(count=60):
+    out = []
+    for s in range(count):
+        n = 4 + s % 9
+        side = 16 if s % 3 == 0 else (1 << 12)
+        kind = "uniform" if s % 2 == 0 else "gmm"
+        if kind == "gmm" and side == 16:
+            kind = "uniform"
+        out.append(meshgen.generate(kind, n, side, 1000 + s))
+    return out
+
+
+TINY = tiny_meshes()
+
+
+# --------------------------------------------------------------------- tests
+@pytest.mark.parametrize("case", GOLDEN, ids=[c["name"] for c in GOLDEN])
+def test_golden(case):
+    pin_golden(case)
+
+
+@pytest.mark.parametrize("k,seed", [(1, 0), (2, 1), (5, 2), (16, 3)])
+def test_grid_closed_form(k, seed):
+    pin_grid(k, seed)
+
+
+@pytest.mark.parametrize("idx", range(len(TINY)))
+def test_bruteforce_tiny(idx):
+    pin_bruteforce(TINY[idx])
+
+
+def test_bruteforce_small_with_tips():
+    """Small Delaunay meshes that do have barrier-edge tips: brute-force labels and
+    regions, then every final-mesh invariant after reparation."""
+    seen = 0
+    for s in range(40):
+        mesh = meshgen.generate("uniform", 300, 1 << 16, 77 + s)
+        r = pin_bruteforce(mesh)
+        seen += r["splits"]
+    assert seen > 0
+
+
+def test_invariants_uniform_1k():
+    mesh = meshgen.load("uniform-1k")
+    r = oracle.full(mesh)
+    polys = csr_to_lists(r["trav_off"], r["trav_vtx"])
+    # before reparation: one polygon per seed, sum of lengths = frontier half-edges
+    assert len(polys) == len(r["seeds"])
+    assert len(r["trav_vtx"]) == int(r["label"]["frontier"].sum())
+    assert any(tips(p) for p in polys)
+    final = csr_to_lists(r["off"], r["vtx"])
+    check_final_mesh(mesh, final, r["frontier_final"])
+    assert not any(tips(p) for p in final)
+    # Section 3.2.3: each split adds one polygon and two vertex slots
+    assert len(final) == len(polys) + r["splits"]
+    assert len(r["vtx"]) == len(r["trav_vtx"]) + 2 * r["splits"]
+
+
+def test_invariants_gmm_20k():
+    mesh = meshgen.generate("gmm", 20_000, 1 << 26, 5)
+    r = oracle.full(mesh)
+    final = csr_to_lists(r["off"], r["vtx"])
+    check_final_mesh(mesh, final, r["frontier_final"])
+    assert len(final) == len(r["seeds"]) + r["splits"]
+
+
+def test_run_matches_phases():
+    mesh = meshgen.load("uniform-1k")
+    a = oracle.full(mesh)
+    b = oracle.run(mesh)
+    assert np.array_equal(a["off"], b["off"]) and np.array_equal(a["vtx"], b["vtx"])
+    assert np.array_equal(a["frontier_final"], b["frontier"])
+    assert np.array_equal(a["label"]["max_edge"], b["max_edge"])
+
+
+# --------------------------------------------------------------------- planted mistakes
+MUTATIONS = {
+    "tie_direction": ("return edge_id(twin, h) < edge_id(twin, g);",
+                      "return edge_id(twin, h) > edge_id(twin, g);"),
+    "tie_ignores_twin": ("return (g >= 0 && g < h) ? g : h;", "return h;"),
+    "frontier_or": ("} else if (!is_longest(max_edge, h) && !is_longest(max_edge, g)) {",
+                    "} else if (!is_longest(max_edge, h) || !is_longest(max_edge, g)) {"),
+    "seed_upper_triangle": ("seed[ta < tb ? ta : tb] = 1;", "seed[ta < tb ? tb : ta] = 1;"),
+    "border_seed_dropped": ("        seed[h / 3] = 1;\n", "        (void)0;\n"),
+    "start_largest_origin": ("if (tri[h] < tri[start] || (tri[h] == tri[start] && h < start)) start = h;",
+                             "if (tri[h] > tri[start] || (tri[h] == tri[start] && h < start)) start = h;"),
+    "middle_floor_plus_one": ("const int64_t j = (k + 1) / 2;", "const int64_t j = k / 2 + 1;"),
+    "middle_cw": ("static int64_t rot_ccw(const int32_t* twin, int64_t o) { return twin[he_prev(o)]; }",
+                  "static int64_t rot_ccw(const int32_t* twin, int64_t o) { return he_next(twin[o]); }"),
+    "halves_swapped": ("int64_t la = region_polygon(c, oj / 3, buf, NULL);",
+                       "int64_t la = region_polygon(c, twin[oj] / 3, buf, NULL);"),
+    "longest_is_shortest": ("if (edge_longer(xy, tri, twin, 3 * t + k, 3 * t + best)) best = k;",
+                            "if (edge_longer(xy, tri, twin, 3 * t + best, 3 * t + k)) best = k;"),
+    "length_dx_only": ("return dx * dx + dy * dy;", "return dx * dx + dy;"),
+}
+
+
+def _run_pins(lib):
+    """Run the pin suite on a given oracle build; returns the names of failed pins."""
+    failed = []
+    for case in GOLDEN:
+        try:
+            pin_golden(case, lib)
+        except Exception:
+            failed.append(case["name"])
+    for k, seed in [(2, 1), (5, 2)]:
+        try:
+            pin_grid(k, seed, lib)
+        except Exception:
+            failed.append(f"grid{k}")
+    for i, mesh in enumerate(TINY[:30]):
+        try:
+            pin_bruteforce(mesh, lib)
+        except Exception:
+            failed.append(f"tiny{i}")
+    return failed
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    src = open(oracle._SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation anchor not found: {name}"
+    mutated = tmp_path / "polylla_oracle.c"
+    mutated.write_text(src.replace(old, new))
+    shutil.copy(oracle._HDR, tmp_path / "polylla_oracle.h")
+    lib = oracle.load_variant(str(mutated), str(tmp_path / f"lib_{name}.so"))
+    failed = _run_pins(lib)
+    assert failed, f"planted mistake '{name}' passed every pin"
+
+
+def test_unmutated_oracle_passes_pin_suite():
+    assert _run_pins(None) == []
