@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the terminal-edge-region mesher on one GB300 (or N replicas).
+
+One step = the whole mesher (Algorithm 1: label, seeds, traversal, reparation)
+over one mesh of the workload, through the C ABI (polylla_run), inputs resident
+in HBM.  Default workload: 10,000,000 lattice points from a 16-component Gaussian
+mixture on a 2^26 grid, exact Delaunay (about 20M triangles).  Its inputs
+(xy 160 MB, tri 240 MB, twin 240 MB) are larger than L2, so no flush is done
+between steps.
+
+Prints one JSON line: triangles/s (device-timed with CUDA events), per-kernel
+times and the HBM roofline of the dominant kernel, the end-to-end figure through
+the host-buffer entry point (copies included), the CPU oracle as a reported
+baseline, clocks sampled during the timed region, and the kernel-launch count.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the oracle (plain sequential C, the only reference there
+is) is timed on the host cores on a bounded sample of the same workload.
+Under torchrun (N > 1) each rank runs an independent replica on its own GPU
+(the path does not shard); the timed region is bracketed by a barrier and the
+max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "triangles/sec end-to-end (device-timed) at 10M pts"
+UNIT = "triangles/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on the gmm16-10m workload, keyed by the hash of the CUDA sources they were taken
+# with; reported as null once the sources change.
+NCU_TRAFFIC = {"sources": None, "bytes": {}}
+
+
+# ------------------------------------------------------------------ helpers
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2204_05438_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(name: str, s: dict) -> float:
+    """Bytes a kernel must move if every element it needs is read or written once
+    (n vertices, m triangles, ns seeds, nv0 / nv traversal / final polygon
+    vertices, np final polygons)."""
+    n, m, ns, nv0, nv, npoly = s["n"], s["m"], s["ns"], s["nv0"], s["nv"], s["np"]
+    return {
+        "label_max": 12 * m + 16 * n + m,                 # tri, xy, Max byte
+        "label_class": 12 * m + m + m,                    # twin, label byte in / out
+        "seed_write": m + 4 * ns,                         # label byte, seed list
+        "trav_count": 4 * ns + 4 * nv0 + 4 * (3 * m - nv0) + m + 16 * ns,
+        "repair_split": 4 * ns,
+        "final_write": 12 * ns + 4 * nv + 4 * (3 * m - nv) + m + 8 * (npoly + 1) + 4 * nv,
+        "trav_write": 8 * ns + 4 * nv0 + 4 * (3 * m - nv0) + m + 8 * (ns + 1) + 4 * nv0,
+    }.get(name, 0.0)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+class Dist:
+    """Replica bookkeeping under torchrun: barrier and max-over-ranks only (gloo)."""
+
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, dist: Dist) -> dict | None:
+    import numpy as np
+    import torch
+
+    import meshgen
+    import paper_2204_05438_gb300 as pg
+
+    torch.cuda.set_device(dist.local_rank)
+    dev = torch.device("cuda", dist.local_rank)
+    mesh = meshgen.load(args.workload)
+    n, m = mesh["xy"].shape[0], mesh["tri"].shape[0]
+    M = pg.from_numpy(mesh, device=str(dev), validate=True)
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up (also yields the output sizes used for the byte counts)
+    for _ in range(args.warmup):
+        M.run(stream)
+    torch.cuda.synchronize(dev)
+    st = M.stats()
+
+    # timed region: K fused steps, CUDA events on the launching stream
+    clocks = ClockSampler(dist.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = pg.launch_count(M.handle)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        M.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    local_ms = e0.elapsed_time(e1)
+    launches = pg.launch_count(M.handle) - launches0
+    clk = clocks.stop()
+    total_ms = dist.max(local_ms)
+    ms_per_step = total_ms / args.steps
+    value = dist.world * m * args.steps / (total_ms / 1e3)
+
+    # per-kernel durations: the same steps with events around every launch
+    pg.set_timing(M.handle, True)
+    for _ in range(args.kernel_steps):
+        M.run(stream)
+    recs = pg.kernel_times(M.handle, reset=True)
+    pg.set_timing(M.handle, False)
+    per = {}
+    for name, ms in recs:
+        per.setdefault(name, []).append(ms)
+    sizes = {"n": n, "m": m, "ns": st["n_seeds"], "nv0": st["n_vtx_trav"], "nv": st["n_vtx"],
+             "np": st["n_poly"]}
+    peak, peak_kind = hbm_peak()
+    kernels = {}
+    step_sum = sum(statistics.mean(v) for v in per.values())
+    for name, v in per.items():
+        avg = statistics.mean(v)
+        b = algorithmic_bytes(name, sizes)
+        gbs = b / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        kernels[name] = {"ms": round(avg, 5), "share": round(avg / step_sum, 4),
+                         "alg_bytes": int(b), "gbs": round(gbs, 1),
+                         "frac": round(gbs / peak, 4)}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    label_seed = [k for k in ("label_max", "label_class", "scan_seeds", "seed_write") if k in kernels]
+    ls_ms = sum(kernels[k]["ms"] for k in label_seed)
+    ls_bytes = sum(kernels[k]["alg_bytes"] for k in label_seed)
+    traffic = None
+    if NCU_TRAFFIC["sources"] == source_hash():
+        traffic = NCU_TRAFFIC["bytes"].get(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["gbs"], "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
+                "traffic": traffic, "alg_bytes_per_launch": kernels[dom]["alg_bytes"]}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        hm = pg.mesh_create_host(n, m)
+        hxy = torch.from_numpy(mesh["xy"]).pin_memory()
+        htri = torch.from_numpy(np.ascontiguousarray(mesh["tri"])).pin_memory()
+        htwin = torch.from_numpy(mesh["twin"]).pin_memory()
+        hoff = torch.empty(m + 1, dtype=torch.int64).pin_memory()
+        hvtx = torch.empty(3 * m, dtype=torch.int32).pin_memory()
+        pg.run_host(hm, hxy, htri, htwin, hoff, hvtx, stream)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            npoly, nvtx = pg.run_host(hm, hxy, htri, htwin, hoff, hvtx, stream)
+        t1 = time.perf_counter()
+        dist.barrier()
+        pg.mesh_destroy(hm)
+        e2e_s = dist.max(t1 - t0)
+        e2e = {"value": dist.world * m * args.e2e_steps / e2e_s, "unit": UNIT,
+               "ms_per_step": 1e3 * e2e_s / args.e2e_steps,
+               "h2d_bytes_per_step": int(16 * n + 24 * m),
+               "d2h_bytes_per_step": int(8 * (npoly + 1) + 4 * nvtx + 8 * 12),
+               "api": "polylla_run_host"}
+
+    M.close()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "points": n, "triangles": m,
+                   "generator": "SplitMix64 16-component Gaussian mixture on a 2^26 lattice, "
+                                "exact Delaunay (seed 2)",
+                   "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (640 MB vs 126 MB); no flush",
+                   "step": "polylla_run: label + seeds + traverse + repair, inputs resident"},
+        "roofline": roofline,
+        "label_seed": {"ms": round(ls_ms, 5), "alg_bytes": int(ls_bytes),
+                       "gbs": round(ls_bytes / (ls_ms * 1e-3) / 1e9, 1) if ls_ms else None,
+                       "frac": round(ls_bytes / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None},
+        "kernels": kernels,
+        "mesh_stats": st,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "sources": source_hash(),
+    }
+    return out
+
+
+def cpu_baseline(mesh_name: str, budget_s: float) -> dict:
+    """The oracle as it stands, one host thread, on the full workload mesh (or a
+    smaller mesh of the same distribution if the full one would exceed the budget)."""
+    import meshgen
+    import oracle
+
+    mesh = meshgen.load(mesh_name)
+    m = mesh["tri"].shape[0]
+    t0 = time.perf_counter()
+    oracle.run(mesh)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full run of {mesh_name} ({m} triangles) in {dt:.2f} s, "
+                      "sequential C, 1 thread"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, dist: Dist) -> dict | None:
+    """The CPU oracle, timed on the host cores, each step one run over a bounded
+    sample of the workload: a mesh of the same distribution (16-component Gaussian
+    mixture on a 2^26 lattice) sized so that warm-up + steps take about two minutes."""
+    import meshgen
+    import oracle
+
+    if dist.rank != 0:
+        return None
+    cfg = meshgen.CONFIGS[args.workload]
+    per_step = max(0.05, 120.0 / max(1, args.steps + args.warmup))
+    sec_per_tri = 1.0 / 1.2e6  # oracle throughput measured on the full workload
+    tri_target = per_step / sec_per_tri
+    n_sample = int(min(cfg["n"], max(2_000, tri_target / 2)))
+    mesh = meshgen.generate(cfg["kind"], n_sample, cfg["side"], cfg["seed"])
+    m = mesh["tri"].shape[0]
+    for _ in range(args.warmup):
+        oracle.run(mesh)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(mesh)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = m * args.steps / total
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sample_points": n_sample, "sample_triangles": m,
+                   "parallelism": "host CPU, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_sample}-point mesh of the {args.workload} distribution "
+                                   f"({m} triangles) per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="gmm16-10m")
+    ap.add_argument("--kernel-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            out = run_reference(args, dist)
+        else:
+            out = run_ours(args, dist)
+            if out is not None and dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+                out["cpu_baseline"] = cpu_baseline(args.workload, 30.0)
+        if out is not None and dist.rank == 0:
+            print(json.dumps(out), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * polylla.h -- C ABI of the GB300 terminal-edge-region polygonal mesher.
+ *
+ * Implements the GPU algorithm of Salinas, Ojeda, Hitschfeld and Ortiz-Bernardin,
+ * "GPU parallel algorithm for the generation of polygonal meshes based on
+ * terminal-edge regions" (IMR 2022): label every edge of a 2D triangulation
+ * (Section 3.2.1, Algorithm 2), build one polygon per terminal-edge region
+ * (Section 3.2.2, Algorithms 3 and 4) and split non-simple polygons at their
+ * barrier-edge tips (Section 3.2.3, Algorithm 5), driven as in Algorithm 1.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Mesh layout (Section 2, with an explicit half-edge twin in place of the
+ * Neighbor array):
+ *   xy   int64[2n]  device; xy[2v], xy[2v+1] = lattice coordinates of vertex v,
+ *                   each in [0, 2^30) (exact int64 squared lengths).
+ *   tri  int32[3m]  device; tri[3t+k] = k-th vertex of triangle t, ccw, with
+ *                   positive area.  Half-edge h = 3t+k runs from tri[h] to
+ *                   tri[3t+(k+1)%3].
+ *   twin int32[3m]  device; the opposite half-edge of h, or -1 on the border.
+ * Sizes: 3 <= n < 2^31, 1 <= m <= 700,000,000 (half-edge ids fit int32).
+ *
+ * Ownership: the input arrays are borrowed, never written, and must stay valid
+ * until polylla_mesh_destroy.  Every derived array (labels, seeds, polygons) is
+ * owned by the handle; pointers returned by the getters stay valid until the
+ * next phase call on the handle or its destruction.
+ *
+ * Ordering: every call is asynchronous on the given stream (a cudaStream_t passed
+ * as void*; NULL = the legacy default stream), except the calls documented as
+ * synchronising.  One handle must not be used from two streams at once.
+ *
+ * Errors: every call returns a polylla_status and never throws.  Errors found on
+ * the device (an index out of range, a walk or reparation exceeding its bound)
+ * are recorded in a per-handle device word and reported by the next
+ * synchronising call.  Phases must run in order label -> seeds -> traverse ->
+ * repair (polylla_label may restart the pipeline at any time), else
+ * POLYLLA_ERR_STATE.
+ *
+ * Label byte lab[t] (one per triangle):
+ *   bits 0-1  index k (0..2) of the longest edge of t (the Max array, Section 2);
+ *             lengths are exact squared lengths, ties go to the edge with the
+ *             lower undirected id min(h, twin(h)) (a reading: the paper gives no
+ *             tie rule);
+ *   bit 2+k   edge k of t is a frontier edge (LabelFrontier, Algorithm 2);
+ *   bit 5     t is a seed triangle (LabelSeed, Algorithm 2; the Seed array);
+ *   bit 6     the longest edge of t is a terminal edge.
+ * An edge that is neither frontier nor terminal is an internal edge.
+ *
+ * Polygons: CSR, int64 off[np+1] and int32 vtx[off[np]]; polygon i is
+ * vtx[off[i] .. off[i+1]), ccw, starting at its frontier half-edge with the
+ * smallest (origin vertex, half-edge id) -- i.e. at its smallest vertex id once
+ * simple.  After traversal polygon i belongs to the i-th seed in ascending
+ * order; reparation replaces each split polygon, in place, by its two halves
+ * (recursively), the half containing the new half-edge tip->x first.
+ */
+#ifndef POLYLLA_H
+#define POLYLLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct polylla_mesh* polylla_mesh_t;
+
+typedef enum {
+  POLYLLA_OK = 0,
+  POLYLLA_ERR_INVALID_ARG = 1, /* null pointer, bad size, unknown flag */
+  POLYLLA_ERR_RANGE = 2,       /* coordinate outside [0, 2^30), id out of range */
+  POLYLLA_ERR_TOPOLOGY = 3,    /* twin not consistent, triangle not ccw / degenerate */
+  POLYLLA_ERR_OOM = 4,         /* device allocation failed */
+  POLYLLA_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+  POLYLLA_ERR_LIMIT = 6,       /* a walk or a reparation exceeded its bound */
+  POLYLLA_ERR_STATE = 7        /* phase called out of order */
+} polylla_status;
+
+#define POLYLLA_VALIDATE 1u /* mesh_create checks the mesh on the device (synchronises) */
+
+#define POLYLLA_LAB_MAX_MASK 0x03u
+#define POLYLLA_LAB_FRONTIER_SHIFT 2
+#define POLYLLA_LAB_SEED 0x20u
+#define POLYLLA_LAB_TERMINAL 0x40u
+
+/* Statistics of the last completed pipeline (polylla_get_stats). */
+typedef struct {
+  int64_t n_seeds;        /* seeds = terminal-edge regions */
+  int64_t n_poly_trav;    /* polygons after traversal (= n_seeds) */
+  int64_t n_vtx_trav;     /* their total length (= frontier half-edges) */
+  int64_t n_tip_polygons; /* polygons with at least one barrier-edge tip */
+  int64_t n_tips;         /* barrier-edge tips found by traversal */
+  int64_t n_splits;       /* splits made by reparation */
+  int64_t n_poly;         /* polygons after reparation */
+  int64_t n_vtx;          /* their total length */
+} polylla_stats;
+
+/*
+ * Create a handle over a device-resident triangulation (Section 2's arrays).
+ * d_xy, d_tri, d_twin: device pointers as described above (borrowed).  d_twin
+ * must not be NULL.  flags: 0 or POLYLLA_VALIDATE; with VALIDATE the mesh is
+ * checked on the device (ids and twins in range, twin an involution between
+ * reversed edges, coordinates in range, every triangle ccw with positive area)
+ * and the call synchronises with `stream`.  Allocates every derived buffer
+ * (about 60 bytes per triangle) so that later phases allocate nothing.
+ * On success *out receives the handle; on failure *out is NULL.
+ */
+polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, const int32_t* d_tri,
+                                   int64_t n_tri, const int32_t* d_twin, uint32_t flags,
+                                   void* stream, polylla_mesh_t* out);
+
+/*
+ * Label phase (Section 3.2.1, Algorithm 2): LabelMax, then LabelSeed and
+ * LabelFrontier fused in one pass, writing lab[m] (layout above).  Restarts the
+ * pipeline.  Asynchronous.
+ */
+polylla_status polylla_label(polylla_mesh_t mesh, void* stream);
+
+/*
+ * Seeds (Section 3.2.1, the Seed array): the seed triangles compacted in
+ * ascending order into a device int32 list, with its length kept on the device.
+ * Asynchronous.
+ */
+polylla_status polylla_seeds(polylla_mesh_t mesh, void* stream);
+
+/*
+ * Traversal phase (Section 3.2.2, Algorithms 3 and 4): one polygon per seed, in
+ * seed order, written as CSR (the Mesh and Position arrays) at offsets given by a
+ * scan instead of the paper's atomicAdd.  Polygons may be non-simple.
+ * Asynchronous.
+ */
+polylla_status polylla_traverse(polylla_mesh_t mesh, void* stream);
+
+/*
+ * Reparation phase (Section 3.2.3, Algorithm 5 with the loop of Algorithm 1):
+ * every polygon with barrier-edge tips is split at its smallest tip vertex along
+ * the middle internal edge e_ceil(k/2) (k internal edges at the tip, counted ccw
+ * after the barrier edge), which becomes a frontier edge in lab[], repeatedly
+ * until no tips remain.  Writes the final CSR.  Asynchronous.
+ */
+polylla_status polylla_repair(polylla_mesh_t mesh, void* stream);
+
+/*
+ * Algorithm 1 end to end: label, seeds, traversal and reparation.  The final
+ * polygons and labels equal those of the four phase calls; the pre-reparation
+ * CSR is not materialised.  Asynchronous.
+ */
+polylla_status polylla_run(polylla_mesh_t mesh, void* stream);
+
+/* Device pointer to lab[m] (valid after polylla_label; updated by repair). */
+polylla_status polylla_get_labels(polylla_mesh_t mesh, const uint8_t** d_lab);
+
+/* Device pointer to the seed list and its length.  Synchronises. */
+polylla_status polylla_get_seeds(polylla_mesh_t mesh, const int32_t** d_seeds, int64_t* n_seeds);
+
+/* Device pointers to the latest CSR (after traverse: pre-reparation; after
+ * repair or run: final) and its sizes.  Synchronises. */
+polylla_status polylla_get_polygons(polylla_mesh_t mesh, const int64_t** d_off,
+                                    const int32_t** d_vtx, int64_t* n_poly, int64_t* n_vtx);
+
+/* Statistics of the pipeline so far (fields of later phases are 0).  Synchronises. */
+polylla_status polylla_get_stats(polylla_mesh_t mesh, polylla_stats* out);
+
+/* Release every buffer of the handle (synchronises with the device). */
+polylla_status polylla_mesh_destroy(polylla_mesh_t mesh);
+
+/* Static, human-readable name of a status. */
+const char* polylla_status_str(polylla_status status);
+
+/*
+ * End-to-end call from HOST memory: copies xy, tri, twin from host buffers
+ * (pinned memory recommended) into device buffers owned by `mesh`, runs
+ * polylla_run, and copies the final CSR back into host buffers.  `mesh` must
+ * have been created with polylla_mesh_create_host.  h_off needs room for
+ * n_tri+1 entries and h_vtx for 3*n_tri (the bounds of the final mesh).
+ * Synchronises.
+ */
+polylla_status polylla_mesh_create_host(int64_t n_vertices, int64_t n_tri, polylla_mesh_t* out);
+polylla_status polylla_run_host(polylla_mesh_t mesh, const int64_t* h_xy, const int32_t* h_tri,
+                                const int32_t* h_twin, int64_t* h_off, int32_t* h_vtx,
+                                int64_t* n_poly, int64_t* n_vtx, void* stream);
+
+/*
+ * Per-kernel timing: when enabled, every kernel the handle launches is bracketed
+ * by CUDA events on its stream.  polylla_kernel_times fills up to `cap` entries
+ * (name, milliseconds) of the launches since the last reset, synchronising, and
+ * returns the number of launches recorded.  polylla_launch_count returns the
+ * number of kernels launched by the handle since creation.
+ */
+polylla_status polylla_set_timing(polylla_mesh_t mesh, int enable);
+int64_t polylla_kernel_times(polylla_mesh_t mesh, const char** names, float* ms, int64_t cap,
+                             int reset);
+int64_t polylla_launch_count(polylla_mesh_t mesh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYLLA_H */

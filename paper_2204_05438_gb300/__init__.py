@@ -1,0 +1,301 @@
+"""GB300-native terminal-edge-region polygonal mesher (Python binding).
+
+Argument marshalling only: every step of the mesher runs in the CUDA kernels of
+``libpolylla.so`` (sources in ``csrc/``, C ABI in ``include/polylla.h``).  PyTorch
+provides device memory and streams.  The functions mirror the C entry points:
+
+    mesh_create, label, seeds, traverse, repair, run, get_labels, get_seeds,
+    get_polygons, get_stats, mesh_destroy, status_str, mesh_create_host,
+    run_host, set_timing, kernel_times, launch_count
+
+There is no CPU fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+VALIDATE = 1
+LAB_MAX_MASK = 0x03
+LAB_FRONTIER_SHIFT = 2
+LAB_SEED = 0x20
+LAB_TERMINAL = 0x40
+
+STATUS = {0: "POLYLLA_OK", 1: "POLYLLA_ERR_INVALID_ARG", 2: "POLYLLA_ERR_RANGE",
+          3: "POLYLLA_ERR_TOPOLOGY", 4: "POLYLLA_ERR_OOM", 5: "POLYLLA_ERR_CUDA",
+          6: "POLYLLA_ERR_LIMIT", 7: "POLYLLA_ERR_STATE"}
+
+
+class PolyllaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "n_seeds", "n_poly_trav", "n_vtx_trav", "n_tip_polygons", "n_tips", "n_splits",
+        "n_poly", "n_vtx")]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load (building it first if needed) the CUDA library.  Raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if path is None and not os.path.exists(p):
+            _build.build()
+        if not os.path.exists(p):
+            raise ImportError(f"libpolylla not found at {p}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(p)
+        vp, i64, u32, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int
+        st = ctypes.c_int
+        sig = {
+            "polylla_mesh_create": ([vp, i64, vp, i64, vp, u32, vp, ctypes.POINTER(vp)], st),
+            "polylla_label": ([vp, vp], st),
+            "polylla_seeds": ([vp, vp], st),
+            "polylla_traverse": ([vp, vp], st),
+            "polylla_repair": ([vp, vp], st),
+            "polylla_run": ([vp, vp], st),
+            "polylla_get_labels": ([vp, ctypes.POINTER(vp)], st),
+            "polylla_get_seeds": ([vp, ctypes.POINTER(vp), ctypes.POINTER(i64)], st),
+            "polylla_get_polygons": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
+            "polylla_get_stats": ([vp, ctypes.POINTER(Stats)], st),
+            "polylla_mesh_destroy": ([vp], st),
+            "polylla_status_str": ([st], ctypes.c_char_p),
+            "polylla_mesh_create_host": ([i64, i64, ctypes.POINTER(vp)], st),
+            "polylla_run_host": ([vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64),
+                                  ctypes.POINTER(i64), vp], st),
+            "polylla_set_timing": ([vp, i32], st),
+            "polylla_kernel_times": ([vp, ctypes.POINTER(ctypes.c_char_p),
+                                      ctypes.POINTER(ctypes.c_float), i64, i32], i64),
+            "polylla_launch_count": ([vp], i64),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise PolyllaError(code, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dptr(t: torch.Tensor, dtype: torch.dtype, name: str) -> int:
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t.data_ptr()
+
+
+class _DeviceArray:
+    """A borrowed device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr) if n else 0, False), "version": 3,
+                                         "strides": None}
+
+
+def _view(ptr: int, n: int, typestr: str, dtype: torch.dtype) -> torch.Tensor:
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, n, typestr), device="cuda")
+
+
+# ------------------------------------------------------------------ C-ABI mirror
+def mesh_create(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor, flags: int = VALIDATE,
+                stream=None) -> int:
+    """polylla_mesh_create: xy int64 [n,2], tri int32 [m,3], twin int32 [3m] on the GPU."""
+    lib = load_library()
+    n = xy.numel() // 2
+    m = tri.numel() // 3
+    h = ctypes.c_void_p()
+    _check(lib.polylla_mesh_create(_dptr(xy, torch.int64, "xy"), n, _dptr(tri, torch.int32, "tri"),
+                                   m, _dptr(twin, torch.int32, "twin"), flags, _stream(stream),
+                                   ctypes.byref(h)), "polylla_mesh_create")
+    return h.value
+
+
+def label(mesh: int, stream=None):
+    _check(load_library().polylla_label(mesh, _stream(stream)), "polylla_label")
+
+
+def seeds(mesh: int, stream=None):
+    _check(load_library().polylla_seeds(mesh, _stream(stream)), "polylla_seeds")
+
+
+def traverse(mesh: int, stream=None):
+    _check(load_library().polylla_traverse(mesh, _stream(stream)), "polylla_traverse")
+
+
+def repair(mesh: int, stream=None):
+    _check(load_library().polylla_repair(mesh, _stream(stream)), "polylla_repair")
+
+
+def run(mesh: int, stream=None):
+    _check(load_library().polylla_run(mesh, _stream(stream)), "polylla_run")
+
+
+def get_labels(mesh: int, m: int) -> torch.Tensor:
+    """View of the handle's label bytes (uint8 [m]); valid until the next phase call."""
+    p = ctypes.c_void_p()
+    _check(load_library().polylla_get_labels(mesh, ctypes.byref(p)), "polylla_get_labels")
+    return _view(p.value, m, "|u1", torch.uint8)
+
+
+def get_seeds(mesh: int) -> torch.Tensor:
+    p, n = ctypes.c_void_p(), ctypes.c_int64()
+    _check(load_library().polylla_get_seeds(mesh, ctypes.byref(p), ctypes.byref(n)),
+           "polylla_get_seeds")
+    return _view(p.value, n.value, "<i4", torch.int32)
+
+
+def get_polygons(mesh: int):
+    """Views (off int64 [np+1], vtx int32 [nv]) of the latest CSR polygons."""
+    po, pv = ctypes.c_void_p(), ctypes.c_void_p()
+    npoly, nv = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().polylla_get_polygons(mesh, ctypes.byref(po), ctypes.byref(pv),
+                                               ctypes.byref(npoly), ctypes.byref(nv)),
+           "polylla_get_polygons")
+    off = torch.as_tensor(_DeviceArray(po.value, npoly.value + 1, "<i8"), device="cuda")
+    return off, _view(pv.value, nv.value, "<i4", torch.int32)
+
+
+def get_stats(mesh: int) -> dict:
+    s = Stats()
+    _check(load_library().polylla_get_stats(mesh, ctypes.byref(s)), "polylla_get_stats")
+    return s.as_dict()
+
+
+def mesh_destroy(mesh: int):
+    _check(load_library().polylla_mesh_destroy(mesh), "polylla_mesh_destroy")
+
+
+def status_str(code: int) -> str:
+    return load_library().polylla_status_str(code).decode()
+
+
+def mesh_create_host(n_vertices: int, n_tri: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().polylla_mesh_create_host(n_vertices, n_tri, ctypes.byref(h)),
+           "polylla_mesh_create_host")
+    return h.value
+
+
+def run_host(mesh: int, xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
+             off_out: torch.Tensor, vtx_out: torch.Tensor, stream=None):
+    """polylla_run_host on (preferably pinned) CPU tensors; returns (n_poly, n_vtx)."""
+    for t, name in ((xy, "xy"), (tri, "tri"), (twin, "twin"), (off_out, "off"), (vtx_out, "vtx")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    npoly, nv = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().polylla_run_host(mesh, xy.data_ptr(), tri.data_ptr(), twin.data_ptr(),
+                                           off_out.data_ptr(), vtx_out.data_ptr(),
+                                           ctypes.byref(npoly), ctypes.byref(nv),
+                                           _stream(stream)), "polylla_run_host")
+    return npoly.value, nv.value
+
+
+def set_timing(mesh: int, enable: bool = True):
+    _check(load_library().polylla_set_timing(mesh, int(enable)), "polylla_set_timing")
+
+
+def kernel_times(mesh: int, reset: bool = True, cap: int = 1 << 16):
+    """[(kernel name, ms)] of the launches timed since the last reset."""
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_float * cap)()
+    k = load_library().polylla_kernel_times(mesh, names, ms, cap, int(reset))
+    if k < 0:
+        raise PolyllaError(5, "polylla_kernel_times")
+    return [(names[i].decode(), float(ms[i])) for i in range(min(k, cap))]
+
+
+def launch_count(mesh: int) -> int:
+    return int(load_library().polylla_launch_count(mesh))
+
+
+# ------------------------------------------------------------------ convenience
+class Mesh:
+    """Owns a handle over device tensors (kept alive here) and runs the phases."""
+
+    def __init__(self, xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
+                 validate: bool = True, stream=None):
+        self.xy, self.tri, self.twin = xy, tri, twin
+        self.m = tri.numel() // 3
+        self.handle = mesh_create(xy, tri, twin, VALIDATE if validate else 0, stream)
+
+    def label(self, stream=None):
+        label(self.handle, stream)
+
+    def seeds(self, stream=None):
+        seeds(self.handle, stream)
+
+    def traverse(self, stream=None):
+        traverse(self.handle, stream)
+
+    def repair(self, stream=None):
+        repair(self.handle, stream)
+
+    def run(self, stream=None):
+        run(self.handle, stream)
+
+    def labels(self) -> torch.Tensor:
+        return get_labels(self.handle, self.m)
+
+    def seed_list(self) -> torch.Tensor:
+        return get_seeds(self.handle)
+
+    def polygons(self):
+        return get_polygons(self.handle)
+
+    def stats(self) -> dict:
+        return get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_numpy(mesh: dict, device: str = "cuda", validate: bool = True, stream=None) -> Mesh:
+    """Upload a generated mesh dict (xy, tri, twin numpy arrays) and create a handle."""
+    xy = torch.as_tensor(mesh["xy"]).to(device=device, dtype=torch.int64).contiguous()
+    tri = torch.as_tensor(mesh["tri"]).to(device=device, dtype=torch.int32).contiguous()
+    twin = torch.as_tensor(mesh["twin"]).to(device=device, dtype=torch.int32).contiguous()
+    return Mesh(xy, tri, twin, validate=validate, stream=stream)

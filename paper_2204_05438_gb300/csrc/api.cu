@@ -1,0 +1,522 @@
+// C ABI of the mesher (declared in include/polylla.h): handle, buffers, phase
+// sequencing, getters, host-buffer entry point and per-kernel timing.
+//
+// Every buffer is allocated once by polylla_mesh_create (sizes are bounded by the
+// triangle count m: at most m seeds and polygons, at most 3m polygon vertices, at
+// most m reparation pieces), so no phase allocates, synchronises or copies to the
+// host; phases only enqueue kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "polylla_internal.cuh"
+
+using namespace polylla;
+
+namespace {
+
+enum Phase { kCreated = 0, kLabeled, kSeeded, kTraversed, kRepaired };
+
+struct TimingRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct polylla_mesh {
+  DevMesh M;
+  int device = 0;
+  int sms = 148;
+  bool owns_inputs = false;
+  int phase = kCreated;
+  int latest_csr = -1;  // 0: traversal CSR, 1: final CSR
+  cudaStream_t last_stream = nullptr;
+
+  uint8_t* lab = nullptr;
+  int* seeds = nullptr;
+  int* p_start = nullptr;
+  int* p_len = nullptr;
+  int* p_tip = nullptr;
+  int* p_ntip = nullptr;
+  int* p_pbase = nullptr;
+  int* p_pcnt = nullptr;
+  int* piece_start = nullptr;
+  int* piece_len = nullptr;
+  long long piece_cap = 0;
+  long long* tile_sum = nullptr;
+  long long* tile_off = nullptr;
+  long long* off_trav = nullptr;
+  int* vtx_trav = nullptr;
+  long long* off_final = nullptr;
+  int* vtx_final = nullptr;
+  Counters* C = nullptr;
+
+  bool timing = false;
+  std::vector<TimingRec> recs;
+  std::vector<cudaEvent_t> event_pool;
+  long long launches = 0;
+};
+
+namespace {
+
+polylla_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return POLYLLA_OK;
+  if (e == cudaErrorMemoryAllocation) return POLYLLA_ERR_OOM;
+  return POLYLLA_ERR_CUDA;
+}
+
+cudaEvent_t take_event(polylla_mesh* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch one kernel through `fn`, bracketed by events when timing is on.
+template <class F>
+polylla_status launch(polylla_mesh* h, const char* name, cudaStream_t s, F fn) {
+  TimingRec r{name, nullptr, nullptr};
+  if (h->timing) {
+    r.a = take_event(h);
+    r.b = take_event(h);
+    if (r.a) cudaEventRecord(r.a, s);
+  }
+  cudaError_t e = fn();
+  ++h->launches;
+  if (h->timing) {
+    if (r.b) cudaEventRecord(r.b, s);
+    if (r.a && r.b) h->recs.push_back(r);
+  }
+  return cuda_status(e);
+}
+
+#define POLY_TRY(expr)                        \
+  do {                                        \
+    polylla_status _st = (expr);              \
+    if (_st != POLYLLA_OK) return _st;        \
+  } while (0)
+
+int grid_for(const polylla_mesh* h, long long units, int per_block) {
+  long long blocks = (units + per_block - 1) / per_block;
+  long long cap = (long long)h->sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, long long count) {
+  if (count < 1) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)count);
+}
+
+void free_all(polylla_mesh* h) {
+  void* ptrs[] = {h->lab,       h->seeds,     h->p_start,  h->p_len,    h->p_tip,
+                  h->p_ntip,    h->p_pbase,   h->p_pcnt,   h->piece_start, h->piece_len,
+                  h->tile_sum,  h->tile_off,  h->off_trav, h->vtx_trav, h->off_final,
+                  h->vtx_final, h->C};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->owns_inputs) {
+    cudaFree(const_cast<long long*>(h->M.xy));
+    cudaFree(const_cast<int*>(h->M.tri));
+    cudaFree(const_cast<int*>(h->M.twin));
+  }
+  for (auto& r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : h->event_pool) cudaEventDestroy(e);
+}
+
+polylla_status alloc_derived(polylla_mesh* h) {
+  const long long m = h->M.m;
+  const long long ntiles_tri = (m + kTriTile - 1) / kTriTile;
+  const long long ntiles_poly = (m + kPolyTile - 1) / kPolyTile;
+  const long long ntiles = ntiles_tri > ntiles_poly ? ntiles_tri : ntiles_poly;
+  h->piece_cap = m + 1;
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, cnt) \
+  if (e == cudaSuccess) e = dalloc(&(ptr), (cnt))
+  ALLOC(h->lab, m + 4);
+  ALLOC(h->seeds, m);
+  ALLOC(h->p_start, m);
+  ALLOC(h->p_len, m);
+  ALLOC(h->p_tip, m);
+  ALLOC(h->p_ntip, m);
+  ALLOC(h->p_pbase, m);
+  ALLOC(h->p_pcnt, m);
+  ALLOC(h->piece_start, h->piece_cap);
+  ALLOC(h->piece_len, h->piece_cap);
+  ALLOC(h->tile_sum, 2 * ntiles);
+  ALLOC(h->tile_off, 2 * ntiles);
+  ALLOC(h->off_trav, m + 1);
+  ALLOC(h->vtx_trav, 3 * m);
+  ALLOC(h->off_final, m + 1);
+  ALLOC(h->vtx_final, 3 * m);
+  ALLOC(h->C, 1);
+#undef ALLOC
+  if (e == cudaSuccess) e = cudaMemset(h->C, 0, sizeof(Counters));
+  return cuda_status(e);
+}
+
+polylla_status read_counters(polylla_mesh* h, Counters* out) {
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  if (e == cudaSuccess) e = cudaMemcpy(out, h->C, sizeof(Counters), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (out->error) return (polylla_status)out->error;
+  return POLYLLA_OK;
+}
+
+polylla_status check_handle(polylla_mesh* h) {
+  if (!h) return POLYLLA_ERR_INVALID_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return POLYLLA_ERR_CUDA;
+  if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return POLYLLA_ERR_CUDA;
+  return POLYLLA_OK;
+}
+
+// ---------------------------------------------------------------- phases
+polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
+  const DevMesh& M = h->M;
+  POLY_TRY(cuda_status(cudaMemsetAsync(h->C, 0, sizeof(Counters), s)));
+  const int g1 = grid_for(h, (M.m + 3) / 4, kBlock);
+  POLY_TRY(launch(h, "label_max", s, [&] { return launch_label_max(M, h->lab, h->C, g1, s); }));
+  const int g2 = grid_for(h, M.m, kTriTile);
+  POLY_TRY(launch(h, "label_class", s,
+                  [&] { return launch_label_class(M, h->lab, h->tile_sum, h->C, g2, s); }));
+  h->phase = kLabeled;
+  h->latest_csr = -1;
+  return POLYLLA_OK;
+}
+
+polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
+  const DevMesh& M = h->M;
+  POLY_TRY(launch(h, "scan_seeds", s, [&] {
+    return launch_scan_tiles(h->tile_sum, h->tile_off, M.m, nullptr, kTriTile, &h->C->n_seeds,
+                             &h->C->scratch0, nullptr, 0, 0, h->C, s);
+  }));
+  const int g = grid_for(h, M.m, kTriTile);
+  POLY_TRY(launch(h, "seed_write", s,
+                  [&] { return launch_seed_write(h->lab, M.m, h->tile_off, h->seeds, g, s); }));
+  h->phase = kSeeded;
+  return POLYLLA_OK;
+}
+
+polylla_status do_trav_count(polylla_mesh* h, cudaStream_t s) {
+  const int g = grid_for(h, h->M.m, kPolyTile * 4);
+  return launch(h, "trav_count", s, [&] {
+    return launch_trav_count(h->M, h->lab, h->seeds, h->p_start, h->p_len, h->p_tip, h->p_ntip,
+                             h->tile_sum, h->C, g, s);
+  });
+}
+
+polylla_status do_traverse(polylla_mesh* h, cudaStream_t s) {
+  POLY_TRY(do_trav_count(h, s));
+  POLY_TRY(launch(h, "scan_trav", s, [&] {
+    return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
+                             &h->C->scratch0, &h->C->scratch1, h->off_trav, 1, h->M.m, h->C, s);
+  }));
+  const int g = grid_for(h, h->M.m, kPolyTile * 4);
+  POLY_TRY(launch(h, "trav_write", s, [&] {
+    return launch_trav_write(h->M, h->lab, h->p_start, h->p_len, h->tile_off, h->off_trav,
+                             h->vtx_trav, h->C, g, s);
+  }));
+  h->phase = kTraversed;
+  h->latest_csr = 0;
+  return POLYLLA_OK;
+}
+
+polylla_status do_repair(polylla_mesh* h, cudaStream_t s, bool copy_from_trav) {
+  const int g = grid_for(h, h->M.m, kPolyTile * 4);
+  POLY_TRY(launch(h, "repair_split", s, [&] {
+    return launch_repair_split(h->M, h->lab, h->p_start, h->p_len, h->p_tip, h->p_ntip,
+                               h->p_pbase, h->p_pcnt, h->piece_start, h->piece_len, h->piece_cap,
+                               h->tile_sum, h->C, g, s);
+  }));
+  POLY_TRY(launch(h, "scan_final", s, [&] {
+    return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
+                             &h->C->n_poly, &h->C->n_vtx, h->off_final, 2, h->M.m, h->C, s);
+  }));
+  POLY_TRY(launch(h, "final_write", s, [&] {
+    return launch_final_write(h->M, h->lab, h->p_start, h->p_len, h->p_ntip, h->p_pbase,
+                              h->p_pcnt, h->piece_start, h->piece_len, h->tile_off,
+                              copy_from_trav ? h->off_trav : nullptr,
+                              copy_from_trav ? h->vtx_trav : nullptr, h->off_final,
+                              h->vtx_final, h->C, g, s);
+  }));
+  h->phase = kRepaired;
+  h->latest_csr = 1;
+  return POLYLLA_OK;
+}
+
+polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags) {
+  if (cudaGetDevice(&h->device) != cudaSuccess) return POLYLLA_ERR_CUDA;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  POLY_TRY(alloc_derived(h));
+  h->last_stream = s;
+  if (flags & POLYLLA_VALIDATE) {
+    const int g = grid_for(h, (h->M.n > 3 * h->M.m ? h->M.n : 3 * h->M.m), kBlock);
+    POLY_TRY(launch(h, "validate", s, [&] { return launch_validate(h->M, h->C, g, s); }));
+    Counters c;
+    polylla_status st = read_counters(h, &c);
+    if (st != POLYLLA_OK) return st;
+  }
+  return POLYLLA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* polylla_status_str(polylla_status st) {
+  switch (st) {
+    case POLYLLA_OK: return "POLYLLA_OK";
+    case POLYLLA_ERR_INVALID_ARG: return "POLYLLA_ERR_INVALID_ARG";
+    case POLYLLA_ERR_RANGE: return "POLYLLA_ERR_RANGE";
+    case POLYLLA_ERR_TOPOLOGY: return "POLYLLA_ERR_TOPOLOGY";
+    case POLYLLA_ERR_OOM: return "POLYLLA_ERR_OOM";
+    case POLYLLA_ERR_CUDA: return "POLYLLA_ERR_CUDA";
+    case POLYLLA_ERR_LIMIT: return "POLYLLA_ERR_LIMIT";
+    case POLYLLA_ERR_STATE: return "POLYLLA_ERR_STATE";
+  }
+  return "POLYLLA_ERR_UNKNOWN";
+}
+
+polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, const int32_t* d_tri,
+                                   int64_t n_tri, const int32_t* d_twin, uint32_t flags,
+                                   void* stream, polylla_mesh_t* out) {
+  if (!out) return POLYLLA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d_xy || !d_tri || !d_twin) return POLYLLA_ERR_INVALID_ARG;
+  if (n_vertices < 3 || n_vertices > 0x7fffffffll || n_tri < 1 || n_tri > 700000000ll)
+    return POLYLLA_ERR_INVALID_ARG;
+  if ((flags & ~POLYLLA_VALIDATE) != 0) return POLYLLA_ERR_INVALID_ARG;
+  if (((uintptr_t)d_xy | (uintptr_t)d_tri | (uintptr_t)d_twin) & 15u) return POLYLLA_ERR_INVALID_ARG;
+  polylla_mesh* h = new (std::nothrow) polylla_mesh();
+  if (!h) return POLYLLA_ERR_OOM;
+  h->M.xy = reinterpret_cast<const long long*>(d_xy);
+  h->M.tri = d_tri;
+  h->M.twin = d_twin;
+  h->M.n = n_vertices;
+  h->M.m = n_tri;
+  polylla_status st = create_common(h, (cudaStream_t)stream, flags);
+  if (st != POLYLLA_OK) {
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_mesh_create_host(int64_t n_vertices, int64_t n_tri, polylla_mesh_t* out) {
+  if (!out) return POLYLLA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_vertices < 3 || n_vertices > 0x7fffffffll || n_tri < 1 || n_tri > 700000000ll)
+    return POLYLLA_ERR_INVALID_ARG;
+  polylla_mesh* h = new (std::nothrow) polylla_mesh();
+  if (!h) return POLYLLA_ERR_OOM;
+  long long* xy = nullptr;
+  int *tri = nullptr, *twin = nullptr;
+  cudaError_t e = dalloc(&xy, 2 * n_vertices);
+  if (e == cudaSuccess) e = dalloc(&tri, 3 * n_tri);
+  if (e == cudaSuccess) e = dalloc(&twin, 3 * n_tri);
+  h->owns_inputs = true;
+  h->M.xy = xy;
+  h->M.tri = tri;
+  h->M.twin = twin;
+  h->M.n = n_vertices;
+  h->M.m = n_tri;
+  polylla_status st = cuda_status(e);
+  if (st == POLYLLA_OK) st = create_common(h, nullptr, 0);
+  if (st != POLYLLA_OK) {
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_label(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  h->last_stream = (cudaStream_t)stream;
+  return do_label(h, (cudaStream_t)stream);
+}
+
+polylla_status polylla_seeds(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  if (h->phase != kLabeled) return POLYLLA_ERR_STATE;
+  h->last_stream = (cudaStream_t)stream;
+  return do_seeds(h, (cudaStream_t)stream);
+}
+
+polylla_status polylla_traverse(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  if (h->phase != kSeeded) return POLYLLA_ERR_STATE;
+  h->last_stream = (cudaStream_t)stream;
+  return do_traverse(h, (cudaStream_t)stream);
+}
+
+polylla_status polylla_repair(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  if (h->phase != kTraversed) return POLYLLA_ERR_STATE;
+  h->last_stream = (cudaStream_t)stream;
+  return do_repair(h, (cudaStream_t)stream, true);
+}
+
+polylla_status polylla_run(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  POLY_TRY(do_label(h, s));
+  POLY_TRY(do_seeds(h, s));
+  POLY_TRY(do_trav_count(h, s));
+  return do_repair(h, s, false);
+}
+
+polylla_status polylla_get_labels(polylla_mesh_t h, const uint8_t** d_lab) {
+  POLY_TRY(check_handle(h));
+  if (!d_lab) return POLYLLA_ERR_INVALID_ARG;
+  if (h->phase < kLabeled) return POLYLLA_ERR_STATE;
+  *d_lab = h->lab;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_get_seeds(polylla_mesh_t h, const int32_t** d_seeds, int64_t* n_seeds) {
+  POLY_TRY(check_handle(h));
+  if (!d_seeds || !n_seeds) return POLYLLA_ERR_INVALID_ARG;
+  if (h->phase < kSeeded) return POLYLLA_ERR_STATE;
+  Counters c;
+  POLY_TRY(read_counters(h, &c));
+  *d_seeds = h->seeds;
+  *n_seeds = c.n_seeds;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_get_polygons(polylla_mesh_t h, const int64_t** d_off, const int32_t** d_vtx,
+                                    int64_t* n_poly, int64_t* n_vtx) {
+  POLY_TRY(check_handle(h));
+  if (!d_off || !d_vtx || !n_poly || !n_vtx) return POLYLLA_ERR_INVALID_ARG;
+  if (h->latest_csr < 0) return POLYLLA_ERR_STATE;
+  Counters c;
+  POLY_TRY(read_counters(h, &c));
+  if (h->latest_csr == 0) {
+    *d_off = reinterpret_cast<const int64_t*>(h->off_trav);
+    *d_vtx = h->vtx_trav;
+    *n_poly = c.n_seeds;
+    *n_vtx = c.n_vtx_trav;
+  } else {
+    *d_off = reinterpret_cast<const int64_t*>(h->off_final);
+    *d_vtx = h->vtx_final;
+    *n_poly = c.n_poly;
+    *n_vtx = c.n_vtx;
+  }
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_get_stats(polylla_mesh_t h, polylla_stats* out) {
+  POLY_TRY(check_handle(h));
+  if (!out) return POLYLLA_ERR_INVALID_ARG;
+  Counters c;
+  POLY_TRY(read_counters(h, &c));
+  std::memset(out, 0, sizeof(*out));
+  if (h->phase >= kSeeded) out->n_seeds = c.n_seeds;
+  if (h->phase >= kTraversed || h->latest_csr == 1) {
+    out->n_poly_trav = c.n_seeds;
+    out->n_vtx_trav = c.n_vtx_trav;
+    out->n_tip_polygons = c.n_tip_polys;
+    out->n_tips = c.n_tips;
+  }
+  if (h->phase >= kRepaired) {
+    out->n_splits = c.n_splits;
+    out->n_poly = c.n_poly;
+    out->n_vtx = c.n_vtx;
+  }
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_mesh_destroy(polylla_mesh_t h) {
+  if (!h) return POLYLLA_ERR_INVALID_ARG;
+  POLY_TRY(check_handle(h));
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_run_host(polylla_mesh_t h, const int64_t* h_xy, const int32_t* h_tri,
+                                const int32_t* h_twin, int64_t* h_off, int32_t* h_vtx,
+                                int64_t* n_poly, int64_t* n_vtx, void* stream) {
+  POLY_TRY(check_handle(h));
+  if (!h->owns_inputs) return POLYLLA_ERR_STATE;
+  if (!h_xy || !h_tri || !h_twin || !h_off || !h_vtx || !n_poly || !n_vtx)
+    return POLYLLA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = h->M.n, m = h->M.m;
+  cudaError_t e =
+      cudaMemcpyAsync(const_cast<long long*>(h->M.xy), h_xy, sizeof(long long) * 2 * n,
+                      cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<int*>(h->M.tri), h_tri, sizeof(int) * 3 * m,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<int*>(h->M.twin), h_twin, sizeof(int) * 3 * m,
+                        cudaMemcpyHostToDevice, s);
+  POLY_TRY(cuda_status(e));
+  POLY_TRY(polylla_run(h, stream));
+  Counters c;
+  POLY_TRY(read_counters(h, &c));
+  e = cudaMemcpyAsync(h_off, h->off_final, sizeof(long long) * (size_t)(c.n_poly + 1),
+                      cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_vtx, h->vtx_final, sizeof(int) * (size_t)c.n_vtx, cudaMemcpyDeviceToHost,
+                        s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  POLY_TRY(cuda_status(e));
+  *n_poly = c.n_poly;
+  *n_vtx = c.n_vtx;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_set_timing(polylla_mesh_t h, int enable) {
+  POLY_TRY(check_handle(h));
+  h->timing = enable != 0;
+  return POLYLLA_OK;
+}
+
+int64_t polylla_kernel_times(polylla_mesh_t h, const char** names, float* ms, int64_t cap,
+                             int reset) {
+  if (check_handle(h) != POLYLLA_OK) return -1;
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return -1;
+  const int64_t n = (int64_t)h->recs.size();
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    if (names) names[i] = h->recs[(size_t)i].name;
+    if (ms) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, h->recs[(size_t)i].a, h->recs[(size_t)i].b);
+      ms[i] = t;
+    }
+  }
+  if (reset) {
+    for (auto& r : h->recs) {
+      h->event_pool.push_back(r.a);
+      h->event_pool.push_back(r.b);
+    }
+    h->recs.clear();
+  }
+  return n;
+}
+
+int64_t polylla_launch_count(polylla_mesh_t h) { return h ? h->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,348 @@
+// Label phase (Section 3.2.1, Algorithm 2) and seed compaction.
+//
+//   k_label_max    LabelMax: per triangle, the index of its longest edge.
+//   k_label_class  LabelSeed + LabelFrontier fused: per triangle, the frontier
+//                  flag of each edge, "longest edge is terminal" and the seed
+//                  flag, plus the seed count of every 1024-triangle tile.
+//   k_seed_write   the Seed array compacted in ascending order (tile offsets
+//                  come from the scan of the tile counts).
+//
+// All three are HBM streams over the triangle arrays (tri / twin: 12 bytes per
+// triangle each, read as 3 x int4 per thread of 4 triangles) with gathers of
+// vertex coordinates (LabelMax) or of neighbour label bytes (LabelSeed /
+// LabelFrontier) that hit L2 on spatially ordered meshes.  Every id read from the
+// input is range-checked before it is dereferenced; a bad id sets the handle's
+// error word and the element is skipped.
+#include "polylla_internal.cuh"
+
+namespace polylla {
+
+// ------------------------------------------------------------------ validation
+__global__ void __launch_bounds__(kBlock) k_validate(DevMesh M, Counters* C) {
+  const long long n = M.n, m = M.m, H = 3 * m;
+  const long long lim = n > H ? n : H;
+  const long long kMaxCoord = 1ll << 30;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < lim;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < n) {
+      const long long x = M.xy[2 * i], y = M.xy[2 * i + 1];
+      if (x < 0 || x >= kMaxCoord || y < 0 || y >= kMaxCoord) set_error(C, POLYLLA_ERR_RANGE, 1);
+    }
+    if (i < H) {
+      const int h = (int)i;
+      const int v = M.tri[h];
+      const int w = M.tri[he_next(h)];
+      if (v < 0 || v >= n) {
+        set_error(C, POLYLLA_ERR_RANGE, 2);
+      }
+      const int g = M.twin[h];
+      if (g < -1 || g >= H) {
+        set_error(C, POLYLLA_ERR_RANGE, 3);
+      } else if (g >= 0) {
+        if (g == h || M.twin[g] != h || M.tri[g] != w || M.tri[he_next(g)] != v)
+          set_error(C, POLYLLA_ERR_TOPOLOGY, 4);
+      }
+    }
+    if (i < m) {
+      const int a = M.tri[3 * i], b = M.tri[3 * i + 1], c = M.tri[3 * i + 2];
+      if (a < 0 || a >= n || b < 0 || b >= n || c < 0 || c >= n) continue;  // reported above
+      const long long ax = M.xy[2 * a], ay = M.xy[2 * a + 1];
+      const long long bx = M.xy[2 * b], by = M.xy[2 * b + 1];
+      const long long cx = M.xy[2 * c], cy = M.xy[2 * c + 1];
+      if (ax < 0 || ax >= kMaxCoord || ay < 0 || ay >= kMaxCoord || bx < 0 || bx >= kMaxCoord ||
+          by < 0 || by >= kMaxCoord || cx < 0 || cx >= kMaxCoord || cy < 0 || cy >= kMaxCoord)
+        continue;  // reported by the vertex check
+      const long long orient = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+      if (orient <= 0) set_error(C, POLYLLA_ERR_TOPOLOGY, 5);
+    }
+  }
+}
+
+cudaError_t launch_validate(const DevMesh& M, Counters* C, int grid, cudaStream_t s) {
+  k_validate<<<grid, kBlock, 0, s>>>(M, C);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ loads
+// The 12 ints of triangles 4g .. 4g+3 (3 x int4 when the group is complete;
+// scalar loads, zero-filled, for the ragged last group).
+__device__ __forceinline__ void load_tri_group(const int* __restrict__ a, long long g, long long m,
+                                               int v[12]) {
+  const long long t0 = 4 * g;
+  if (t0 + 4 <= m) {
+    const int4* p = reinterpret_cast<const int4*>(a) + 3 * g;
+    const int4 x = __ldg(p), y = __ldg(p + 1), z = __ldg(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+    v[8] = z.x; v[9] = z.y; v[10] = z.z; v[11] = z.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) v[j] = (3 * t0 + j < 3 * m) ? __ldg(a + 3 * t0 + j) : 0;
+  }
+}
+
+__device__ __forceinline__ long long sqdist(longlong2 p, longlong2 q) {
+  const long long dx = q.x - p.x, dy = q.y - p.y;
+  return dx * dx + dy * dy;
+}
+
+// ------------------------------------------------------------------ LabelMax
+// Longest edge by (exact squared length, then lower undirected id min(h, twin(h))).
+// The twin array is read only for triangles whose longest length is tied.
+__global__ void __launch_bounds__(kBlock) k_label_max(DevMesh M, uint8_t* __restrict__ lab,
+                                                      Counters* C) {
+  const long long m = M.m, n = M.n;
+  const long long ngroups = (m + 3) / 4;
+  const longlong2* __restrict__ xy2 = reinterpret_cast<const longlong2*>(M.xy);
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ngroups;
+       g += (long long)gridDim.x * blockDim.x) {
+    int v[12];
+    load_tri_group(M.tri, g, m, v);
+    unsigned packed = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long t = 4 * g + j;
+      if (t >= m) break;
+      const int a = v[3 * j], b = v[3 * j + 1], c = v[3 * j + 2];
+      if ((unsigned)a >= (unsigned long long)n || (unsigned)b >= (unsigned long long)n ||
+          (unsigned)c >= (unsigned long long)n) {
+        set_error(C, POLYLLA_ERR_RANGE, 10);
+        continue;
+      }
+      const longlong2 pa = __ldg(xy2 + a), pb = __ldg(xy2 + b), pc = __ldg(xy2 + c);
+      const long long l0 = sqdist(pa, pb), l1 = sqdist(pb, pc), l2 = sqdist(pc, pa);
+      const long long lmax = max(l0, max(l1, l2));
+      const int cnt = (l0 == lmax) + (l1 == lmax) + (l2 == lmax);
+      int k;
+      if (cnt == 1) {
+        k = (l0 == lmax) ? 0 : ((l1 == lmax) ? 1 : 2);
+      } else {
+        // tie at the maximum: the lower undirected edge id wins
+        const long long l[3] = {l0, l1, l2};
+        int best_e = 0x7fffffff;
+        k = 0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          if (l[e] != lmax) continue;
+          const int h = (int)(3 * t + e);
+          const int tw = __ldg(M.twin + h);
+          const int eid = (tw >= 0 && tw < h) ? tw : h;
+          if (eid < best_e) {
+            best_e = eid;
+            k = e;
+          }
+        }
+      }
+      packed |= (unsigned)k << (8 * j);
+    }
+    const long long t0 = 4 * g;
+    if (t0 + 4 <= m) {
+      reinterpret_cast<unsigned*>(lab)[g] = packed;
+    } else {
+      for (int j = 0; t0 + j < m; ++j) lab[t0 + j] = (uint8_t)(packed >> (8 * j));
+    }
+  }
+}
+
+cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int grid,
+                             cudaStream_t s) {
+  k_label_max<<<grid, kBlock, 0, s>>>(M, lab, C);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ LabelSeed + LabelFrontier
+// Per triangle t with longest edge k* and twins g_k:
+//   frontier(k)  <=> g_k < 0  or  (k != k*  and  edge g_k is not the longest of its triangle)
+//   terminal     <=> g_k* < 0 or  edge g_k* is the longest of its triangle
+//   seed         <=> terminal and (g_k* < 0 or t < triangle(g_k*))
+// Neighbour label bytes are read while other threads rewrite them; only their
+// bits 0-1 (the Max array, written by the previous kernel) are used, and every
+// rewrite keeps those bits.
+__global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
+                                                        long long* __restrict__ tile_sum,
+                                                        Counters* C) {
+  __shared__ int sh[kBlock / 32];
+  const long long m = M.m;
+  const long long H = 3 * m;
+  const long long ntiles = (m + kTriTile - 1) / kTriTile;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long g = tile * kBlock + threadIdx.x;  // group of 4 triangles
+    const long long t0 = 4 * g;
+    int nseed = 0;
+    if (t0 < m) {
+      int tw[12];
+      load_tri_group(M.twin, g, m, tw);
+      const bool full = t0 + 4 <= m;
+      unsigned own = 0;
+      if (full) {
+        own = *reinterpret_cast<const volatile unsigned*>(lab + t0);
+      } else {
+        for (int j = 0; t0 + j < m; ++j) own |= (unsigned)lab[t0 + j] << (8 * j);
+      }
+      unsigned out = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long t = t0 + j;
+        if (t >= m) break;
+        const int kst = (own >> (8 * j)) & 3;
+        unsigned byte = (unsigned)kst;
+        unsigned nbm = 0;  // bit k: edge k is also the longest edge of the neighbour
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int gk = tw[3 * j + k];
+          if (gk >= 0) {
+            if (gk >= H) {
+              set_error(C, POLYLLA_ERR_RANGE, 11);
+              continue;
+            }
+            const int gt = gk / 3;
+            const int nb = *(reinterpret_cast<const volatile uint8_t*>(lab) + gt) & 3;
+            nbm |= (unsigned)(nb == gk - 3 * gt) << k;
+          }
+          const bool fr = (gk < 0) || (k != kst && !((nbm >> k) & 1u));
+          byte |= (unsigned)fr << (2 + k);
+        }
+        const int gs = (kst == 0) ? tw[3 * j] : ((kst == 1) ? tw[3 * j + 1] : tw[3 * j + 2]);
+        const bool terminal = (gs < 0) || ((nbm >> kst) & 1u);
+        const bool seed = terminal && (gs < 0 || t < gs / 3);
+        byte |= (unsigned)terminal << 6;
+        byte |= (unsigned)seed << 5;
+        nseed += seed;
+        out |= byte << (8 * j);
+      }
+      if (full) {
+        *reinterpret_cast<volatile unsigned*>(lab + t0) = out;
+      } else {
+        for (int j = 0; t0 + j < m; ++j)
+          *(reinterpret_cast<volatile uint8_t*>(lab) + t0 + j) = (uint8_t)(out >> (8 * j));
+      }
+    }
+    const int tot = block_sum(nseed, sh);
+    if (threadIdx.x == 0) {
+      tile_sum[2 * tile] = tot;
+      tile_sum[2 * tile + 1] = 0;
+    }
+  }
+}
+
+cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, Counters* C,
+                               int grid, cudaStream_t s) {
+  k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tile_sum, C);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ seed compaction
+__global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict__ lab, long long m,
+                                                       const long long* __restrict__ tile_off,
+                                                       int* __restrict__ seeds) {
+  __shared__ int sh[kBlock / 32];
+  const long long ntiles = (m + kTriTile - 1) / kTriTile;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long t0 = 4 * (tile * kBlock + threadIdx.x);
+    unsigned own = 0;
+    if (t0 + 4 <= m) {
+      own = __ldg(reinterpret_cast<const unsigned*>(lab + t0));
+    } else {
+      for (int j = 0; t0 + j < m; ++j) own |= (unsigned)__ldg(lab + t0 + j) << (8 * j);
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cnt += (own >> (8 * j + 5)) & 1;
+    int tot;
+    int pos = block_exclusive_scan(cnt, &tot, sh);
+    const long long base = tile_off[2 * tile] + pos;
+    int w = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((own >> (8 * j + 5)) & 1) seeds[base + w++] = (int)(t0 + j);
+  }
+}
+
+cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
+                              int* seeds, int grid, cudaStream_t s) {
+  k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, tile_off, seeds);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ tile scan
+// One block: exclusive scan of the per-tile pairs (thread i owns a contiguous
+// run of tiles), with the totals and the optional CSR end marker.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(
+    const long long* __restrict__ tile_sum, long long* __restrict__ tile_off, long long n_host,
+    const long long* n_dev, int tile, long long* tot0, long long* tot1, long long* end,
+    int end_mode, long long end_cap, Counters* C) {
+  __shared__ long long sh0[32], sh1[32];
+  const long long n = n_dev ? *n_dev : n_host;
+  const long long ntiles = (n + tile - 1) / tile;
+  const long long per = (ntiles + kScanThreads - 1) / kScanThreads;
+  const long long lo = threadIdx.x * per;
+  const long long hi = min(lo + per, ntiles);
+  long long s0 = 0, s1 = 0;
+  for (long long i = lo; i < hi; ++i) {
+    s0 += tile_sum[2 * i];
+    s1 += tile_sum[2 * i + 1];
+  }
+  // block scan of (s0, s1) over 1024 threads
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long x0 = s0, x1 = s1;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    long long y0 = __shfl_up_sync(0xffffffffu, x0, d), y1 = __shfl_up_sync(0xffffffffu, x1, d);
+    if (lane >= d) {
+      x0 += y0;
+      x1 += y1;
+    }
+  }
+  if (lane == 31) {
+    sh0[warp] = x0;
+    sh1[warp] = x1;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    long long w0 = sh0[lane], w1 = sh1[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      long long y0 = __shfl_up_sync(0xffffffffu, w0, d), y1 = __shfl_up_sync(0xffffffffu, w1, d);
+      if (lane >= d) {
+        w0 += y0;
+        w1 += y1;
+      }
+    }
+    sh0[lane] = w0;
+    sh1[lane] = w1;
+  }
+  __syncthreads();
+  long long p0 = (warp ? sh0[warp - 1] : 0) + x0 - s0;
+  long long p1 = (warp ? sh1[warp - 1] : 0) + x1 - s1;
+  for (long long i = lo; i < hi; ++i) {
+    tile_off[2 * i] = p0;
+    tile_off[2 * i + 1] = p1;
+    p0 += tile_sum[2 * i];
+    p1 += tile_sum[2 * i + 1];
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    const long long t0 = sh0[31], t1 = sh1[31];
+    if (tot0) *tot0 = t0;
+    if (tot1) *tot1 = t1;
+    const long long at = (end_mode == 1) ? n : t0;
+    const long long val = (end_mode == 1) ? t0 : t1;
+    if (end_mode != 0) {
+      if (at >= 0 && at <= end_cap) {
+        end[at] = val;
+      } else {
+        set_error(C, POLYLLA_ERR_LIMIT, 40);
+      }
+    }
+  }
+}
+
+cudaError_t launch_scan_tiles(const long long* tile_sum, long long* tile_off, long long n_host,
+                              const long long* n_dev, int tile, long long* tot0, long long* tot1,
+                              long long* end, int end_mode, long long end_cap, Counters* C,
+                              cudaStream_t s) {
+  k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_sum, tile_off, n_host, n_dev, tile, tot0, tot1, end,
+                                          end_mode, end_cap, C);
+  return cudaGetLastError();
+}
+
+}  // namespace polylla

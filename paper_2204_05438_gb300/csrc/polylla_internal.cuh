@@ -1,0 +1,140 @@
+// Internal declarations of the GB300 mesher library: device-side data, half-edge
+// helpers, block-level scans and the launchers of every kernel.
+//
+// Mesh layout (Section 2 of the paper, with an explicit half-edge twin): half-edge
+// h = 3t+k of triangle t runs from tri[h] to tri[3t+(k+1)%3]; twin[h] is the
+// opposite half-edge or -1.  The label byte of triangle t packs the Max array
+// (bits 0-1), the frontier flag of each edge (bits 2-4), the Seed array (bit 5)
+// and "the longest edge is terminal" (bit 6).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "polylla.h"
+
+namespace polylla {
+
+constexpr int kBlock = 256;                    // threads per block, every kernel
+constexpr int kTriPerThread = 4;               // label kernels: 4 triangles = 3 x int4
+constexpr int kTriTile = kBlock * kTriPerThread;  // 1024 triangles per seed-count tile
+constexpr int kPolyTile = kBlock;              // walk kernels: one polygon per thread
+constexpr int kScanThreads = 1024;
+
+// Device-resident counters of one pipeline run (zeroed by the label phase).
+struct Counters {
+  long long n_seeds;
+  long long n_vtx_trav;   // total length of the traversal polygons
+  long long n_tip_polys;  // polygons with >= 1 barrier-edge tip
+  long long n_tips;
+  long long n_splits;
+  long long n_poly;       // final polygons
+  long long n_vtx;        // final total length
+  long long piece_alloc;  // reparation scratch cursor
+  long long scratch0;     // scan totals that are not reported
+  long long scratch1;
+  int error;              // first device error (polylla_status), 0 if none
+  int err_info;
+};
+
+struct DevMesh {
+  const long long* xy;  // 2n
+  const int* tri;       // 3m
+  const int* twin;      // 3m
+  long long n, m;
+};
+
+// ----------------------------------------------------------------- half-edges
+__device__ __forceinline__ int he_tri(int h) { return h / 3; }
+__device__ __forceinline__ int he_next(int h) {
+  const int t3 = 3 * (h / 3);
+  return (h - t3 == 2) ? t3 : h + 1;
+}
+__device__ __forceinline__ int he_prev(int h) {
+  const int t3 = 3 * (h / 3);
+  return (h == t3) ? t3 + 2 : h - 1;
+}
+// Frontier flag of half-edge h read from the label byte of its triangle.  Plain
+// loads: reparation updates label bytes inside the same kernel.
+__device__ __forceinline__ bool lab_frontier(const uint8_t* lab, int h) {
+  const int t = h / 3;
+  return (lab[t] >> (2 + (h - 3 * t))) & 1;
+}
+
+__device__ __forceinline__ void set_error(Counters* c, int code, int info) {
+  if (atomicCAS(&c->error, 0, code) == 0) c->err_info = info;
+}
+
+// ----------------------------------------------------------------- block scans
+// Exclusive scan over the kBlock threads of a block; returns the thread's prefix
+// and writes the block total.  `sh` needs kBlock/32 entries.  Contains barriers:
+// every thread of the block must call it.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = (lane < kBlock / 32) ? sh[lane] : T(0);
+#pragma unroll
+    for (int d = 1; d < kBlock / 32; d <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < kBlock / 32) sh[lane] = w;
+  }
+  __syncthreads();
+  const T before = warp ? sh[warp - 1] : T(0);
+  *total = sh[kBlock / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  T tot;
+  block_exclusive_scan(v, &tot, sh);
+  return tot;
+}
+
+// ----------------------------------------------------------------- launchers
+// Every launcher enqueues one kernel on `s` and returns the launch error.
+cudaError_t launch_validate(const DevMesh& M, Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int grid,
+                             cudaStream_t s);
+cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, Counters* C,
+                               int grid, cudaStream_t s);
+cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
+                              int* seeds, int grid, cudaStream_t s);
+// Exclusive scan of per-tile pairs.  Tile count = ceil(n / tile) with n = *n_dev if
+// n_dev, else n_host.  Totals go to *tot0, *tot1.  end_mode 1: end[n] = total0;
+// end_mode 2: end[total0] = total1 (index checked against end_cap).
+cudaError_t launch_scan_tiles(const long long* tile_sum, long long* tile_off, long long n_host,
+                              const long long* n_dev, int tile, long long* tot0, long long* tot1,
+                              long long* end, int end_mode, long long end_cap, Counters* C,
+                              cudaStream_t s);
+cudaError_t launch_trav_count(const DevMesh& M, const uint8_t* lab, const int* seeds,
+                              int* p_start, int* p_len, int* p_tip, int* p_ntip,
+                              long long* tile_sum, Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_trav_write(const DevMesh& M, const uint8_t* lab, const int* p_start,
+                              const int* p_len, const long long* tile_off, long long* off,
+                              int* vtx, Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_repair_split(const DevMesh& M, uint8_t* lab, const int* p_start,
+                                const int* p_len, const int* p_tip, const int* p_ntip,
+                                int* p_pbase, int* p_pcnt, int* piece_start, int* piece_len,
+                                long long piece_cap, long long* tile_sum, Counters* C, int grid,
+                                cudaStream_t s);
+cudaError_t launch_final_write(const DevMesh& M, const uint8_t* lab, const int* p_start,
+                               const int* p_len, const int* p_ntip, const int* p_pbase,
+                               const int* p_pcnt, const int* piece_start, const int* piece_len,
+                               const long long* tile_off, const long long* off_trav,
+                               const int* vtx_trav, long long* off, int* vtx, Counters* C,
+                               int grid, cudaStream_t s);
+
+}  // namespace polylla

@@ -1,0 +1,71 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/polylla.h declares.  Host-only calls only (no GPU needed)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2204_05438_gb300 as pg
+from paper_2204_05438_gb300 import build as pbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "polylla.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(polylla_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return ctypes.CDLL(pbuild.LIB)
+
+
+def test_header_declares_the_pipeline():
+    names = declared_functions()
+    for required in ("polylla_mesh_create", "polylla_label", "polylla_seeds", "polylla_traverse",
+                     "polylla_repair", "polylla_get_polygons", "polylla_mesh_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_covers_every_entry_point():
+    for n in declared_functions():
+        assert hasattr(pg, n[len("polylla_"):]), f"no Python binding for {n}"
+
+
+def test_status_strings():
+    lib = pg.load_library()
+    for code, name in pg.STATUS.items():
+        assert lib.polylla_status_str(code).decode() == name
+
+
+def test_argument_errors_need_no_device():
+    lib = pg.load_library()
+    h = ctypes.c_void_p(123)
+    # null output pointer / null inputs / bad sizes are rejected before any CUDA call
+    assert lib.polylla_mesh_create(None, 10, None, 10, None, 0, None, None) == 1
+    assert lib.polylla_mesh_create(None, 10, None, 10, None, 0, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.polylla_mesh_create(16, 2, 16, 10, 16, 0, None, ctypes.byref(h)) == 1
+    assert lib.polylla_mesh_create(16, 10, 16, 10, 16, 8, None, ctypes.byref(h)) == 1
+    assert lib.polylla_mesh_create(20, 10, 16, 10, 16, 0, None, ctypes.byref(h)) == 1  # misaligned
+    assert lib.polylla_label(None, None) == 1
+    assert lib.polylla_mesh_destroy(None) == 1
+    assert lib.polylla_launch_count(None) == -1
+
+
+def test_compiled_for_sm103a_only():
+    flags = pbuild.compile_flags()
+    assert "arch=compute_103a,code=sm_103a" in flags
+    assert sum("arch=" in f for f in flags) == 1
