@@ -192,6 +192,32 @@ int64_t polylla_kernel_times(polylla_mesh_t mesh, const char** names, float* ms,
                              int reset);
 int64_t polylla_launch_count(polylla_mesh_t mesh);
 
+/*
+ * Allocation-free label phase and seed compaction.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory (a host
+ * that owns the whole device heap, or code that must not let cudaMalloc /
+ * cudaFree synchronise the device).  It computes exactly what polylla_label
+ * followed by polylla_seeds computes, without a handle, and allocates nothing:
+ * its only scratch (per-tile seed counts and offsets, and an error word) lives in
+ * a fixed file-scope device array of about 2 MiB, which every GPU that loads the
+ * library holds until the process exits.
+ *   d_xy, n_vertices, d_tri, d_twin, n_tri: the mesh, as for polylla_mesh_create
+ *     (16-byte aligned), with at most 2^26 triangles -- larger meshes are rejected
+ *     with POLYLLA_ERR_INVALID_ARG;
+ *   d_lab: device uint8[n_tri], 4-byte aligned, receives the label bytes;
+ *   d_seeds: device int32[n_tri] (capacity), receives the ascending seed list;
+ *   d_n_seeds: one device int64, 8-byte aligned, receives the seed count.
+ * The first call on a device looks up the scratch array's address for that device
+ * and should be made before any stream capture.  Every call shares the one array
+ * and clears what must start at zero, so calls that overlap on the GPU race and
+ * must be serialised by the caller.  Synchronises with `stream` before returning,
+ * to report device-side errors.
+ */
+polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64_t n_vertices,
+                                           const int32_t* d_tri, const int32_t* d_twin,
+                                           int64_t n_tri, uint8_t* d_lab, int32_t* d_seeds,
+                                           int64_t* d_n_seeds, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,7 +6,7 @@ provides device memory and streams.  The functions mirror the C entry points:
 
     mesh_create, label, seeds, traverse, repair, run, get_labels, get_seeds,
     get_polygons, get_stats, mesh_destroy, status_str, mesh_create_host,
-    run_host, set_timing, kernel_times, launch_count
+    run_host, set_timing, kernel_times, launch_count, label_seeds_noalloc
 
 There is no CPU fallback: if the library cannot be loaded every call raises.
 """
@@ -88,6 +88,7 @@ def load_library(path: str | None = None):
             "polylla_kernel_times": ([vp, ctypes.POINTER(ctypes.c_char_p),
                                       ctypes.POINTER(ctypes.c_float), i64, i32], i64),
             "polylla_launch_count": ([vp], i64),
+            "polylla_label_seeds_noalloc": ([vp, i64, vp, vp, i64, vp, vp, vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -242,6 +243,22 @@ def kernel_times(mesh: int, reset: bool = True, cap: int = 1 << 16):
 
 def launch_count(mesh: int) -> int:
     return int(load_library().polylla_launch_count(mesh))
+
+
+def label_seeds_noalloc(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
+                        lab_out: torch.Tensor, seeds_out: torch.Tensor, n_seeds_out: torch.Tensor,
+                        stream=None):
+    """polylla_label_seeds_noalloc: label bytes, seed list and seed count written
+    into caller-provided device tensors (uint8 [m], int32 [m], int64 [1]); the
+    library allocates nothing.  For callers that cannot allocate device memory."""
+    m = tri.numel() // 3
+    if lab_out.numel() < m or seeds_out.numel() < m or n_seeds_out.numel() < 1:
+        raise ValueError("output tensors are too small")
+    _check(load_library().polylla_label_seeds_noalloc(
+        _dptr(xy, torch.int64, "xy"), xy.numel() // 2, _dptr(tri, torch.int32, "tri"),
+        _dptr(twin, torch.int32, "twin"), m, _dptr(lab_out, torch.uint8, "lab_out"),
+        _dptr(seeds_out, torch.int32, "seeds_out"), _dptr(n_seeds_out, torch.int64, "n_seeds_out"),
+        _stream(stream)), "polylla_label_seeds_noalloc")
 
 
 # ------------------------------------------------------------------ convenience

@@ -1,0 +1,123 @@
+// polylla_label_seeds_noalloc: the label phase and the seed compaction for callers
+// that cannot allocate device memory.
+//
+// Some callers may not call cudaMalloc at all: a host application that carves
+// all of its device memory out of one arena at start-up and forbids further
+// allocation, code that runs where a cudaMalloc / cudaFree would implicitly
+// synchronise the device and stall other work, or a plugin whose host owns the
+// device heap.  The handle-based entry points allocate their scratch in
+// polylla_mesh_create, so they are closed to such callers.  This entry point takes
+// the same computation (LabelMax, the fused LabelSeed / LabelFrontier pass and the
+// ordered seed compaction) and keeps its only scratch -- the per-tile seed counts,
+// their scanned offsets and the error word -- in a file-scope __device__ array of
+// fixed size, so it allocates nothing.  The caller passes the mesh (inputs) and
+// the label bytes, seed list and seed count (outputs).
+//
+// Limits and sharing:
+//   * at most kNoAllocMaxTri = 2^26 triangles; larger meshes are rejected with
+//     POLYLLA_ERR_INVALID_ARG before anything is launched;
+//   * the scratch array (about 2 MiB) is part of the library image: every GPU that
+//     loads the library holds it until the process exits;
+//   * every call on a device uses the same array and leaves its contents behind;
+//     the parts that must start at zero are cleared at the start of each call, so
+//     consecutive calls are independent, but calls that overlap on the GPU (two
+//     streams, or two host threads at once) race on it and must be serialised by
+//     the caller;
+//   * the first call on a device looks up the array's device address (once per
+//     device, with that device current) and should come before any stream capture;
+//   * the call synchronises with `stream` before returning, to report errors that
+//     the kernels found on the device.
+#include <mutex>
+
+#include "polylla_internal.cuh"
+
+using namespace polylla;
+
+namespace {
+
+constexpr long long kNoAllocMaxTri = 1ll << 26;
+constexpr long long kNoAllocTiles = (kNoAllocMaxTri + kTriTile - 1) / kTriTile;
+constexpr size_t kTileBytes = sizeof(long long) * 2 * (size_t)kNoAllocTiles;
+constexpr size_t kCountersOffset = 2 * kTileBytes;
+constexpr size_t kScratchBytes = kCountersOffset + ((sizeof(Counters) + 255) / 256) * 256;
+constexpr int kMaxDevices = 64;
+
+// The whole scratch of this entry point: tile sums, tile offsets, counters.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+unsigned char* g_scratch_dev[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (looked up once per device; the
+// host-side symbol g_noalloc_scratch is not a device address and is never
+// passed to a kernel).
+cudaError_t scratch_for(int dev, unsigned char** out, int* sms) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_sms[dev] = n;
+    g_scratch_dev[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_dev[dev];
+  *sms = g_sms[dev];
+  return cudaSuccess;
+}
+
+int grid_of(int sms, long long units, long long per_block) {
+  long long b = (units + per_block - 1) / per_block;
+  const long long cap = 8ll * sms;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64_t n_vertices,
+                                                      const int32_t* d_tri, const int32_t* d_twin,
+                                                      int64_t n_tri, uint8_t* d_lab,
+                                                      int32_t* d_seeds, int64_t* d_n_seeds,
+                                                      void* stream) {
+  if (!d_xy || !d_tri || !d_twin || !d_lab || !d_seeds || !d_n_seeds)
+    return POLYLLA_ERR_INVALID_ARG;
+  if (n_vertices < 3 || n_vertices > 0x7fffffffll || n_tri < 1) return POLYLLA_ERR_INVALID_ARG;
+  if (n_tri > kNoAllocMaxTri) return POLYLLA_ERR_INVALID_ARG;  // beyond the fixed scratch
+  if (((uintptr_t)d_xy | (uintptr_t)d_tri | (uintptr_t)d_twin) & 15u) return POLYLLA_ERR_INVALID_ARG;
+  if (((uintptr_t)d_lab & 3u) || ((uintptr_t)d_n_seeds & 7u)) return POLYLLA_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return POLYLLA_ERR_CUDA;
+  unsigned char* base = nullptr;
+  int sms = 0;
+  if (scratch_for(dev, &base, &sms) != cudaSuccess) return POLYLLA_ERR_CUDA;
+  long long* tile_sum = reinterpret_cast<long long*>(base);
+  long long* tile_off = reinterpret_cast<long long*>(base + kTileBytes);
+  Counters* C = reinterpret_cast<Counters*>(base + kCountersOffset);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  DevMesh M;
+  M.xy = reinterpret_cast<const long long*>(d_xy);
+  M.tri = d_tri;
+  M.twin = d_twin;
+  M.n = n_vertices;
+  M.m = n_tri;
+  // the error word and counters start at zero; tile sums are fully rewritten
+  cudaError_t e = cudaMemsetAsync(C, 0, sizeof(Counters), s);
+  if (e == cudaSuccess) e = launch_label_max(M, d_lab, C, grid_of(sms, (n_tri + 3) / 4, kBlock), s);
+  if (e == cudaSuccess) e = launch_label_class(M, d_lab, tile_sum, C, grid_of(sms, n_tri, kTriTile), s);
+  if (e == cudaSuccess)
+    e = launch_scan_tiles(tile_sum, tile_off, n_tri, nullptr, kTriTile,
+                          reinterpret_cast<long long*>(d_n_seeds), &C->scratch0, nullptr, 0, 0, C,
+                          s);
+  if (e == cudaSuccess)
+    e = launch_seed_write(d_lab, n_tri, tile_off, d_seeds, grid_of(sms, n_tri, kTriTile), s);
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &C->error, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return POLYLLA_ERR_CUDA;
+  return (polylla_status)err;
+}
