@@ -38,15 +38,11 @@ struct polylla_mesh {
 
   uint8_t* lab = nullptr;
   int* seeds = nullptr;
-  int* p_start = nullptr;
-  int* p_len = nullptr;
-  int* p_tip = nullptr;
-  int* p_ntip = nullptr;
-  int* p_pbase = nullptr;
-  int* p_pcnt = nullptr;
-  int* piece_start = nullptr;
-  int* piece_len = nullptr;
-  long long piece_cap = 0;
+  int* succ = nullptr;
+  PolyArrays P{};
+  TipArrays T{};
+  FinalPieces F{};
+  int epoch = 0;
   long long* tile_sum = nullptr;
   long long* tile_off = nullptr;
   long long* off_trav = nullptr;
@@ -119,10 +115,13 @@ cudaError_t dalloc(T** p, long long count) {
 }
 
 void free_all(polylla_mesh* h) {
-  void* ptrs[] = {h->lab,       h->seeds,     h->p_start,  h->p_len,    h->p_tip,
-                  h->p_ntip,    h->p_pbase,   h->p_pcnt,   h->piece_start, h->piece_len,
-                  h->tile_sum,  h->tile_off,  h->off_trav, h->vtx_trav, h->off_final,
-                  h->vtx_final, h->C};
+  void* ptrs[] = {h->lab,         h->seeds,        h->succ,         h->P.start,     h->P.len,
+                  h->P.ntip,      h->P.tipbase,    h->P.pbase,      h->P.pcnt,      h->P.flen,
+                  h->P.vb,        h->T.h,          h->T.poly,       h->T.o,         h->T.state,
+                  h->T.piece,     h->T.rec_start,  h->T.rec_len,    h->T.pair_src,  h->T.pair_dst,
+                  h->T.cancel_round, h->T.scratch, h->T.vtip,       h->T.chord,     h->F.start,
+                  h->F.len,       h->F.off,        h->tile_sum,     h->tile_off,    h->off_trav,
+                  h->vtx_trav,    h->off_final,    h->vtx_final,    h->C};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_inputs) {
@@ -138,24 +137,42 @@ void free_all(polylla_mesh* h) {
 }
 
 polylla_status alloc_derived(polylla_mesh* h) {
-  const long long m = h->M.m;
+  const long long m = h->M.m, n = h->M.n;
   const long long ntiles_tri = (m + kTriTile - 1) / kTriTile;
   const long long ntiles_poly = (m + kPolyTile - 1) / kPolyTile;
   const long long ntiles = ntiles_tri > ntiles_poly ? ntiles_tri : ntiles_poly;
-  h->piece_cap = m + 1;
+  h->T.cap = n;       // a vertex is the tip of at most one barrier edge
+  h->F.cap = m + 1;   // final polygons <= m
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, cnt) \
   if (e == cudaSuccess) e = dalloc(&(ptr), (cnt))
   ALLOC(h->lab, m + 4);
   ALLOC(h->seeds, m);
-  ALLOC(h->p_start, m);
-  ALLOC(h->p_len, m);
-  ALLOC(h->p_tip, m);
-  ALLOC(h->p_ntip, m);
-  ALLOC(h->p_pbase, m);
-  ALLOC(h->p_pcnt, m);
-  ALLOC(h->piece_start, h->piece_cap);
-  ALLOC(h->piece_len, h->piece_cap);
+  ALLOC(h->succ, 3 * m);
+  ALLOC(h->P.start, m);
+  ALLOC(h->P.len, m);
+  ALLOC(h->P.ntip, m);
+  ALLOC(h->P.tipbase, m);
+  ALLOC(h->P.pbase, m);
+  ALLOC(h->P.pcnt, m);
+  ALLOC(h->P.flen, m);
+  ALLOC(h->P.vb, m);
+  ALLOC(h->T.h, n);
+  ALLOC(h->T.poly, n);
+  ALLOC(h->T.o, n);
+  ALLOC(h->T.state, n);
+  ALLOC(h->T.piece, 2 * n);
+  ALLOC(h->T.rec_start, 2 * n);
+  ALLOC(h->T.rec_len, 2 * n);
+  ALLOC(h->T.pair_src, n);
+  ALLOC(h->T.pair_dst, n);
+  ALLOC(h->T.cancel_round, n);
+  ALLOC(h->T.scratch, 24 * n);
+  ALLOC(h->T.vtip, n);
+  ALLOC(h->T.chord, 3 * m);
+  ALLOC(h->F.start, h->F.cap);
+  ALLOC(h->F.len, h->F.cap);
+  ALLOC(h->F.off, h->F.cap);
   ALLOC(h->tile_sum, 2 * ntiles);
   ALLOC(h->tile_off, 2 * ntiles);
   ALLOC(h->off_trav, m + 1);
@@ -164,6 +181,9 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->vtx_final, 3 * m);
   ALLOC(h->C, 1);
 #undef ALLOC
+  // epoch-tagged maps start empty (epochs start at 1)
+  if (e == cudaSuccess) e = cudaMemset(h->T.vtip, 0, sizeof(long long) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemset(h->T.chord, 0, sizeof(long long) * (size_t)(3 * m));
   if (e == cudaSuccess) e = cudaMemset(h->C, 0, sizeof(Counters));
   return cuda_status(e);
 }
@@ -187,6 +207,12 @@ polylla_status check_handle(polylla_mesh* h) {
 // ---------------------------------------------------------------- phases
 polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   const DevMesh& M = h->M;
+  if (h->epoch >= 0x7ffffff0) {  // epoch-tagged maps: wrap around once in 2^31 runs
+    POLY_TRY(cuda_status(cudaMemsetAsync(h->T.vtip, 0, sizeof(long long) * (size_t)M.n, s)));
+    POLY_TRY(cuda_status(cudaMemsetAsync(h->T.chord, 0, sizeof(long long) * (size_t)(3 * M.m), s)));
+    h->epoch = 0;
+  }
+  ++h->epoch;
   POLY_TRY(cuda_status(cudaMemsetAsync(h->C, 0, sizeof(Counters), s)));
   const int g1 = grid_for(h, (M.m + 3) / 4, kBlock);
   POLY_TRY(launch(h, "label_max", s, [&] { return launch_label_max(M, h->lab, h->C, g1, s); }));
@@ -211,24 +237,34 @@ polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
   return POLYLLA_OK;
 }
 
+// successor of every frontier half-edge, then one walk per seed
 polylla_status do_trav_count(polylla_mesh* h, cudaStream_t s) {
-  const int g = grid_for(h, h->M.m, kPolyTile * 4);
+  const DevMesh& M = h->M;
+  const int gt = grid_for(h, M.m, kBlock);
+  POLY_TRY(launch(h, "succ", s, [&] { return launch_succ(M, h->lab, h->succ, h->C, gt, s); }));
+  const int gp = grid_for(h, M.m, kBlock * 4);
   return launch(h, "trav_count", s, [&] {
-    return launch_trav_count(h->M, h->lab, h->seeds, h->p_start, h->p_len, h->p_tip, h->p_ntip,
-                             h->tile_sum, h->C, g, s);
+    return launch_trav_count(M, h->lab, h->seeds, h->succ, h->P, h->T, h->epoch, h->C, gp, s);
   });
 }
 
 polylla_status do_traverse(polylla_mesh* h, cudaStream_t s) {
+  const DevMesh& M = h->M;
   POLY_TRY(do_trav_count(h, s));
+  const int gt = grid_for(h, M.m, kPolyTile);
+  POLY_TRY(launch(h, "len_tiles", s,
+                  [&] { return launch_len_tiles(h->P.len, h->tile_sum, h->C, gt, s); }));
   POLY_TRY(launch(h, "scan_trav", s, [&] {
     return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
-                             &h->C->scratch0, &h->C->scratch1, h->off_trav, 1, h->M.m, h->C, s);
+                             &h->C->scratch0, &h->C->scratch1, h->off_trav, 1, M.m, h->C, s);
   }));
-  const int g = grid_for(h, h->M.m, kPolyTile * 4);
+  POLY_TRY(launch(h, "trav_offsets", s, [&] {
+    return launch_offsets(h->P.len, h->tile_off, h->off_trav, h->C, gt, s);
+  }));
+  const int gp = grid_for(h, M.m, kBlock * 4);
   POLY_TRY(launch(h, "trav_write", s, [&] {
-    return launch_trav_write(h->M, h->lab, h->p_start, h->p_len, h->tile_off, h->off_trav,
-                             h->vtx_trav, h->C, g, s);
+    return launch_trav_write(M, h->succ, h->P.start, h->P.len, h->off_trav, h->vtx_trav, h->C, gp,
+                             s);
   }));
   h->phase = kTraversed;
   h->latest_csr = 0;
@@ -236,22 +272,37 @@ polylla_status do_traverse(polylla_mesh* h, cudaStream_t s) {
 }
 
 polylla_status do_repair(polylla_mesh* h, cudaStream_t s, bool copy_from_trav) {
-  const int g = grid_for(h, h->M.m, kPolyTile * 4);
-  POLY_TRY(launch(h, "repair_split", s, [&] {
-    return launch_repair_split(h->M, h->lab, h->p_start, h->p_len, h->p_tip, h->p_ntip,
-                               h->p_pbase, h->p_pcnt, h->piece_start, h->piece_len, h->piece_cap,
-                               h->tile_sum, h->C, g, s);
-  }));
+  const DevMesh& M = h->M;
+  const int gtip = grid_for(h, M.n, kBlock * 4);
+  const int gp = grid_for(h, M.m, kBlock * 4);
+  const int gt = grid_for(h, M.m, kPolyTile);
+  POLY_TRY(launch(h, "tip_split", s,
+                  [&] { return launch_tip_split(M, h->lab, h->T, h->epoch, h->C, gtip, s); }));
+  POLY_TRY(launch(h, "tip_resolve", s, [&] { return launch_tip_resolve(h->T, h->C, s); }));
+  POLY_TRY(launch(h, "tip_mark", s,
+                  [&] { return launch_tip_mark(M, h->lab, h->T, h->epoch, h->C, gtip, s); }));
+  POLY_TRY(launch(h, "resucc", s,
+                  [&] { return launch_resucc(M, h->lab, h->succ, h->T, h->C, gtip, s); }));
+  POLY_TRY(launch(h, "piece_walk", s,
+                  [&] { return launch_piece_walk(M, h->succ, h->T, h->epoch, h->C, gtip, s); }));
+  POLY_TRY(launch(h, "poly_order", s,
+                  [&] { return launch_poly_order(M, h->P, h->T, h->F, h->C, gp, s); }));
+  POLY_TRY(launch(h, "final_tiles", s,
+                  [&] { return launch_final_tiles(h->P, h->tile_sum, h->C, gt, s); }));
   POLY_TRY(launch(h, "scan_final", s, [&] {
     return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
-                             &h->C->n_poly, &h->C->n_vtx, h->off_final, 2, h->M.m, h->C, s);
+                             &h->C->n_poly, &h->C->n_vtx, h->off_final, 2, M.m, h->C, s);
   }));
-  POLY_TRY(launch(h, "final_write", s, [&] {
-    return launch_final_write(h->M, h->lab, h->p_start, h->p_len, h->p_ntip, h->p_pbase,
-                              h->p_pcnt, h->piece_start, h->piece_len, h->tile_off,
-                              copy_from_trav ? h->off_trav : nullptr,
-                              copy_from_trav ? h->vtx_trav : nullptr, h->off_final,
-                              h->vtx_final, h->C, g, s);
+  POLY_TRY(launch(h, "final_offsets", s, [&] {
+    return launch_final_offsets(h->P, h->F, h->tile_off, h->off_final, M.m, h->C, gt, s);
+  }));
+  POLY_TRY(launch(h, "final_write_polys", s, [&] {
+    return launch_final_write_polys(M, h->succ, h->P, copy_from_trav ? h->off_trav : nullptr,
+                                    copy_from_trav ? h->vtx_trav : nullptr, h->vtx_final, h->C,
+                                    gp, s);
+  }));
+  POLY_TRY(launch(h, "final_write_pieces", s, [&] {
+    return launch_final_write_pieces(M, h->succ, h->F, h->vtx_final, h->C, gtip, s);
   }));
   h->phase = kRepaired;
   h->latest_csr = 1;

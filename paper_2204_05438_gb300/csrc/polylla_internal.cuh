@@ -18,7 +18,7 @@ namespace polylla {
 constexpr int kBlock = 256;                    // threads per block, every kernel
 constexpr int kTriPerThread = 4;               // label kernels: 4 triangles = 3 x int4
 constexpr int kTriTile = kBlock * kTriPerThread;  // 1024 triangles per seed-count tile
-constexpr int kPolyTile = kBlock;              // walk kernels: one polygon per thread
+constexpr int kPolyTile = kBlock;              // per-polygon scans: one polygon per thread
 constexpr int kScanThreads = 1024;
 
 // Device-resident counters of one pipeline run (zeroed by the label phase).
@@ -30,7 +30,8 @@ struct Counters {
   long long n_splits;
   long long n_poly;       // final polygons
   long long n_vtx;        // final total length
-  long long piece_alloc;  // reparation scratch cursor
+  long long piece_alloc;  // final piece slots handed out
+  long long n_pairs;      // (tip -> tip) split-edge pairs found by reparation
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
   int error;              // first device error (polylla_status), 0 if none
@@ -119,22 +120,76 @@ cudaError_t launch_scan_tiles(const long long* tile_sum, long long* tile_off, lo
                               const long long* n_dev, int tile, long long* tot0, long long* tot1,
                               long long* end, int end_mode, long long end_cap, Counters* C,
                               cudaStream_t s);
+// Per traversal polygon (index = seed order), capacity m.
+struct PolyArrays {
+  int* start;     // canonical start half-edge
+  int* len;       // traversal length
+  int* ntip;      // barrier-edge tips on the cycle
+  int* tipbase;   // first entry of its tips in the tip list
+  int* pbase;     // first final piece slot (polygons with tips)
+  int* pcnt;      // final pieces
+  int* flen;      // total length of the final pieces
+  long long* vb;  // output vertex offset
+};
+
+// Barrier-edge tips (capacity = n vertices), grouped by polygon.
+struct TipArrays {
+  int* h;              // barrier half-edge a->b ending at the tip b
+  int* poly;           // polygon of the tip
+  int* o;              // split half-edge b->x, or -1
+  int* state;          // 1 processed, 0 cancelled
+  int* piece;          // [2 per tip] record naming the piece on each side
+  int* rec_start;      // [2 per tip] canonical start of the named piece
+  int* rec_len;        // [2 per tip] its length
+  int* pair_src;       // (tip -> tip) pairs
+  int* pair_dst;
+  int* cancel_round;
+  int* scratch;        // [24 per tip] per-polygon ordering scratch
+  long long* vtip;     // [n] (epoch << 32 | tip entry) of the vertex's tip
+  long long* chord;    // [3m] (epoch << 32 | record) of split half-edges
+  long long cap;
+};
+
+// Final pieces of split polygons (capacity m + 1).
+struct FinalPieces {
+  int* start;
+  int* len;
+  long long* off;
+  long long cap;
+};
+
+cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, int* succ, Counters* C, int grid,
+                        cudaStream_t s);
 cudaError_t launch_trav_count(const DevMesh& M, const uint8_t* lab, const int* seeds,
-                              int* p_start, int* p_len, int* p_tip, int* p_ntip,
-                              long long* tile_sum, Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_trav_write(const DevMesh& M, const uint8_t* lab, const int* p_start,
-                              const int* p_len, const long long* tile_off, long long* off,
-                              int* vtx, Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_repair_split(const DevMesh& M, uint8_t* lab, const int* p_start,
-                                const int* p_len, const int* p_tip, const int* p_ntip,
-                                int* p_pbase, int* p_pcnt, int* piece_start, int* piece_len,
-                                long long piece_cap, long long* tile_sum, Counters* C, int grid,
-                                cudaStream_t s);
-cudaError_t launch_final_write(const DevMesh& M, const uint8_t* lab, const int* p_start,
-                               const int* p_len, const int* p_ntip, const int* p_pbase,
-                               const int* p_pcnt, const int* piece_start, const int* piece_len,
-                               const long long* tile_off, const long long* off_trav,
-                               const int* vtx_trav, long long* off, int* vtx, Counters* C,
-                               int grid, cudaStream_t s);
+                              const int* succ, const PolyArrays& P, const TipArrays& T, int epoch,
+                              Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_len_tiles(const int* len, long long* tile_sum, Counters* C, int grid,
+                             cudaStream_t s);
+cudaError_t launch_offsets(const int* len, const long long* tile_off, long long* off, Counters* C,
+                           int grid, cudaStream_t s);
+cudaError_t launch_trav_write(const DevMesh& M, const int* succ, const int* start, const int* len,
+                              const long long* off, int* vtx, Counters* C, int grid,
+                              cudaStream_t s);
+cudaError_t launch_tip_split(const DevMesh& M, const uint8_t* lab, const TipArrays& T, int epoch,
+                             Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_tip_resolve(const TipArrays& T, Counters* C, cudaStream_t s);
+cudaError_t launch_tip_mark(const DevMesh& M, uint8_t* lab, const TipArrays& T, int epoch,
+                            Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_resucc(const DevMesh& M, const uint8_t* lab, int* succ, const TipArrays& T,
+                          Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_piece_walk(const DevMesh& M, const int* succ, const TipArrays& T, int epoch,
+                              Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_poly_order(const DevMesh& M, const PolyArrays& P, const TipArrays& T,
+                              const FinalPieces& F, Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_final_tiles(const PolyArrays& P, long long* tile_sum, Counters* C, int grid,
+                               cudaStream_t s);
+cudaError_t launch_final_offsets(const PolyArrays& P, const FinalPieces& F,
+                                 const long long* tile_off, long long* off, long long m,
+                                 Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_final_write_polys(const DevMesh& M, const int* succ, const PolyArrays& P,
+                                     const long long* off_trav, const int* vtx_trav, int* vtx,
+                                     Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_final_write_pieces(const DevMesh& M, const int* succ, const FinalPieces& F,
+                                      int* vtx, Counters* C, int grid, cudaStream_t s);
 
 }  // namespace polylla

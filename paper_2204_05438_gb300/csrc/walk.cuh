@@ -1,40 +1,38 @@
-// The region walk shared by traversal and reparation (Algorithm 4,
+// Region-boundary walks shared by traversal and reparation (Algorithm 4,
 // PolyConstruction, restated on half-edges).
 //
 // From a frontier half-edge h of a terminal-edge region, the next frontier
 // half-edge of the region's boundary is found by turning around the endpoint of
 // h through internal edges:
 //     g = next(h);  while (g is not frontier) g = next(twin(g));
-// The walk stays inside the region (it never crosses a frontier edge), visits
-// the boundary ccw with the region on its left, and each frontier half-edge
-// contributes its origin vertex.  Every step is bounded (3m + 3 in total) and
-// every twin is range-checked, so a corrupt mesh ends in an error, not a hang.
+// The walk stays inside the region (it never crosses a frontier edge), visits the
+// boundary ccw with the region on its left, and each frontier half-edge
+// contributes its origin vertex.
+//
+// The turn is precomputed once per frontier half-edge into succ[h] (k_succ), so a
+// polygon walk is a chase of one dependent load per vertex.  Bit 31 of succ[h]
+// flags a barrier-edge tip: succ(h) == twin(h), i.e. consecutive polygon vertices
+// v_a, v_b, v_a with v_b = dest(h) (Section 3.2.3).  Every loop is bounded and every
+// index range-checked, so a corrupt mesh ends in an error, not a hang.
 #pragma once
 
 #include "polylla_internal.cuh"
 
 namespace polylla {
 
-struct WalkInfo {
-  int start;  // frontier half-edge with the smallest (origin, id): the canonical start
-  int len;    // number of frontier half-edges = polygon length
-  int tip_h;  // barrier half-edge a->b ending at the smallest tip vertex b, or -1
-  int ntips;  // barrier-edge tips (v_a == v_c on consecutive vertices)
-  bool ok;
-};
+constexpr int kTipFlag = 1 << 31;
+constexpr int kSuccMask = 0x7fffffff;
 
-// Next frontier half-edge after h; returns -1 on a bound violation.
-__device__ __forceinline__ int walk_step(const int* __restrict__ tri, const int* __restrict__ twin,
-                                         const uint8_t* lab, int h, int H, long long& steps,
-                                         long long limit) {
-  (void)tri;
+// Next frontier half-edge after h by turning through internal edges, or -1.
+__device__ __forceinline__ int turn_to_frontier(const int* __restrict__ twin, const uint8_t* lab,
+                                                int h, int H, long long limit) {
   int g = he_next(h);
+  long long steps = 0;
   while (!lab_frontier(lab, g)) {
     const int tw = twin[g];
     if ((unsigned)tw >= (unsigned)H || ++steps > limit) return -1;
     g = he_next(tw);
   }
-  if (++steps > limit) return -1;
   return g;
 }
 
@@ -55,79 +53,55 @@ __device__ __forceinline__ int region_entry(const int* __restrict__ twin, const 
   return g;
 }
 
-// Walk the whole boundary cycle through h0: length, canonical start and tips.
-__device__ __forceinline__ WalkInfo walk_cycle(const int* __restrict__ tri,
-                                               const int* __restrict__ twin, const uint8_t* lab,
-                                               int h0, int H, long long limit) {
-  WalkInfo w;
-  w.start = h0;
-  w.len = 0;
-  w.tip_h = -1;
-  w.ntips = 0;
-  w.ok = false;
-  long long steps = 0;
-  int best_o = 0x7fffffff, best_h = 0x7fffffff;
-  int v0 = -1, v1 = -1;
-  int pp_o = -1, p_o = -1, pp_h = -1, p_h = -1;
-  int tip_v = 0x7fffffff;
-  int h = h0;
-  int len = 0;
-  do {
-    const int o = tri[h];
-    if (o < best_o || (o == best_o && h < best_h)) {
-      best_o = o;
-      best_h = h;
-    }
-    if (len >= 2 && pp_o == o) {  // consecutive v_a, v_b, v_c with v_a == v_c
-      ++w.ntips;
-      if (p_o < tip_v) {
-        tip_v = p_o;
-        w.tip_h = pp_h;
-      }
-    }
-    if (len == 0) v0 = o;
-    if (len == 1) v1 = o;
-    pp_o = p_o;
-    pp_h = p_h;
-    p_o = o;
-    p_h = h;
-    ++len;
-    h = walk_step(tri, twin, lab, h, H, steps, limit);
-    if (h < 0) return w;
-  } while (h != h0);
-  if (len >= 3) {  // the two cyclic triples that wrap around the start
-    if (pp_o == v0) {
-      ++w.ntips;
-      if (p_o < tip_v) {
-        tip_v = p_o;
-        w.tip_h = pp_h;
-      }
-    }
-    if (p_o == v1) {
-      ++w.ntips;
-      if (v0 < tip_v) {
-        tip_v = v0;
-        w.tip_h = p_h;
-      }
-    }
-  }
-  w.start = best_h;
-  w.len = len;
-  w.ok = true;
-  return w;
+// Canonical key of a frontier half-edge: (origin vertex, half-edge id).
+__device__ __forceinline__ unsigned long long he_key(const int* __restrict__ tri, int h) {
+  return ((unsigned long long)(unsigned)tri[h] << 32) | (unsigned)h;
 }
 
-// Write the origins of `len` consecutive frontier half-edges starting at h.
-__device__ __forceinline__ bool walk_write(const int* __restrict__ tri, const int* __restrict__ twin,
-                                           const uint8_t* lab, int h, int len, int H,
-                                           long long limit, int* __restrict__ out) {
+struct CycleInfo {
+  int start;  // half-edge with the smallest (origin, id): the canonical start
+  int len;    // number of frontier half-edges = polygon length
+  int ntips;  // barrier-edge tips on the cycle
+  bool ok;
+};
+
+// Walk the succ cycle through h0 (length, canonical start, tip count).  When
+// tip_out is given, the barrier half-edge of every tip is appended to it.
+__device__ __forceinline__ CycleInfo succ_cycle(const int* __restrict__ tri, const int* succ,
+                                                int h0, int H, long long limit, int* tip_out,
+                                                int tip_cap) {
+  CycleInfo c;
+  c.start = h0;
+  c.len = 0;
+  c.ntips = 0;
+  c.ok = false;
+  unsigned long long best = ~0ull;
+  int h = h0;
   long long steps = 0;
-  for (int j = 0; j < len; ++j) {
-    out[j] = tri[h];
-    if (j + 1 < len) {
-      h = walk_step(tri, twin, lab, h, H, steps, limit);
-      if (h < 0) return false;
+  do {
+    const unsigned long long k = he_key(tri, h);
+    if (k < best) best = k;
+    const int s = succ[h];
+    if (s & kTipFlag) {
+      if (tip_out && c.ntips < tip_cap) tip_out[c.ntips] = h;
+      ++c.ntips;
     }
+    ++c.len;
+    h = s & kSuccMask;
+    if ((unsigned)h >= (unsigned)H || ++steps > limit) return c;
+  } while (h != h0);
+  c.start = (int)(best & 0xffffffffu);
+  c.ok = true;
+  return c;
+}
+
+// Write the origins of the `len` half-edges of the succ cycle starting at h.
+__device__ __forceinline__ bool succ_write(const int* __restrict__ tri, const int* succ, int h,
+                                           int len, int H, int* __restrict__ out) {
+  for (int j = 0; j < len; ++j) {
+    if ((unsigned)h >= (unsigned)H) return false;
+    out[j] = tri[h];
+    h = succ[h] & kSuccMask;
   }
   return true;
 }
