@@ -205,6 +205,13 @@ def run_ours(args, dist: Dist) -> dict | None:
     value = dist.world * m * args.steps / (total_ms / 1e3)
 
     # per-kernel durations: the same steps with events around every launch
+    if args.kernel_steps <= 0:
+        M.close()
+        return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic", "config": {"workload": args.workload},
+                "roofline": None, "gpu_launches": launches, "clocks": clk}
     pg.set_timing(M.handle, True)
     for _ in range(args.kernel_steps):
         M.run(stream)

@@ -38,6 +38,8 @@ CONFIGS = {
     "uniform-1k": dict(kind="uniform", n=1_000, side=1 << 20, seed=0),
     "uniform-1m": dict(kind="uniform", n=1_000_000, side=1 << 24, seed=1),
     "gmm16-10m": dict(kind="gmm", n=10_000_000, side=1 << 26, seed=2),
+    # half-size case of the same distribution, for profiler captures
+    "gmm16-5m": dict(kind="gmm", n=5_000_000, side=1 << 26, seed=2),
 }
 
 

@@ -39,6 +39,12 @@ struct polylla_mesh {
   uint8_t* lab = nullptr;
   int* seeds = nullptr;
   int* succ = nullptr;
+  int* tf = nullptr;      // twin | frontier bit, per half-edge (written by the label phase)
+  int* visit = nullptr;   // per triangle: BFS stamp of the long-polygon blocks
+  int* loc = nullptr;     // per half-edge: member index inside a long-polygon block
+  LongList Lg{};
+  LongMembers LM{};
+  LongMembers LM2{};
   PolyArrays P{};
   TipArrays T{};
   FinalPieces F{};
@@ -121,7 +127,10 @@ void free_all(polylla_mesh* h) {
                   h->T.piece,     h->T.rec_start,  h->T.rec_len,    h->T.pair_src,  h->T.pair_dst,
                   h->T.cancel_round, h->T.scratch, h->T.vtip,       h->T.chord,     h->F.start,
                   h->F.len,       h->F.off,        h->tile_sum,     h->tile_off,    h->off_trav,
-                  h->vtx_trav,    h->off_final,    h->vtx_final,    h->C};
+                  h->vtx_trav,    h->off_final,    h->vtx_final,    h->C,           h->tf,
+                  h->visit,       h->loc,          h->Lg.poly,      h->LM.h,        h->LM.poly,
+                  h->LM2.h,       h->LM2.poly,     h->LM2.rank,     h->P.mode,      h->P.lmbase,
+                  h->F.src,       h->T.rec_slot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_inputs) {
@@ -180,7 +189,24 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->off_final, m + 1);
   ALLOC(h->vtx_final, 3 * m);
   ALLOC(h->C, 1);
+  ALLOC(h->tf, 3 * m);
+  ALLOC(h->visit, m);
+  ALLOC(h->loc, 3 * m);
+  ALLOC(h->Lg.poly, m);
+  ALLOC(h->LM.h, 3 * m);
+  ALLOC(h->LM.poly, 3 * m);
+  ALLOC(h->LM2.h, 3 * m);
+  ALLOC(h->LM2.poly, 3 * m);
+  ALLOC(h->LM2.rank, 3 * m);
+  ALLOC(h->P.mode, m);
+  ALLOC(h->P.lmbase, m);
+  ALLOC(h->F.src, h->F.cap);
+  ALLOC(h->T.rec_slot, 2 * n);
 #undef ALLOC
+  h->Lg.cap = m;
+  h->LM.cap = 3 * m;
+  h->LM2.cap = 3 * m;
+  if (e == cudaSuccess) e = cudaMemset(h->visit, 0, sizeof(int) * (size_t)m);
   // epoch-tagged maps start empty (epochs start at 1)
   if (e == cudaSuccess) e = cudaMemset(h->T.vtip, 0, sizeof(long long) * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(h->T.chord, 0, sizeof(long long) * (size_t)(3 * m));
@@ -210,6 +236,7 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   if (h->epoch >= 0x7ffffff0) {  // epoch-tagged maps: wrap around once in 2^31 runs
     POLY_TRY(cuda_status(cudaMemsetAsync(h->T.vtip, 0, sizeof(long long) * (size_t)M.n, s)));
     POLY_TRY(cuda_status(cudaMemsetAsync(h->T.chord, 0, sizeof(long long) * (size_t)(3 * M.m), s)));
+    POLY_TRY(cuda_status(cudaMemsetAsync(h->visit, 0, sizeof(int) * (size_t)M.m, s)));
     h->epoch = 0;
   }
   ++h->epoch;
@@ -218,7 +245,7 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   POLY_TRY(launch(h, "label_max", s, [&] { return launch_label_max(M, h->lab, h->C, g1, s); }));
   const int g2 = grid_for(h, M.m, kTriTile);
   POLY_TRY(launch(h, "label_class", s,
-                  [&] { return launch_label_class(M, h->lab, h->tile_sum, h->C, g2, s); }));
+                  [&] { return launch_label_class(M, h->lab, h->tile_sum, h->tf, h->C, g2, s); }));
   h->phase = kLabeled;
   h->latest_csr = -1;
   return POLYLLA_OK;
@@ -241,10 +268,15 @@ polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
 polylla_status do_trav_count(polylla_mesh* h, cudaStream_t s) {
   const DevMesh& M = h->M;
   const int gt = grid_for(h, M.m, kBlock);
-  POLY_TRY(launch(h, "succ", s, [&] { return launch_succ(M, h->lab, h->succ, h->C, gt, s); }));
+  POLY_TRY(launch(h, "succ", s, [&] { return launch_succ(M, h->tf, h->succ, h->C, gt, s); }));
   const int gp = grid_for(h, M.m, kBlock * 4);
-  return launch(h, "trav_count", s, [&] {
-    return launch_trav_count(M, h->lab, h->seeds, h->succ, h->P, h->T, h->epoch, h->C, gp, s);
+  POLY_TRY(launch(h, "trav_count", s, [&] {
+    return launch_trav_count(M, h->lab, h->seeds, h->succ, h->P, h->T, h->Lg, h->epoch, h->C, gp,
+                             s);
+  }));
+  return launch(h, "long_trav", s, [&] {
+    return launch_long_trav(M, h->tf, h->seeds, h->succ, h->P, h->T, h->Lg, h->LM, h->visit,
+                            h->loc, h->epoch, h->C, 2 * h->sms, s);
   });
 }
 
@@ -263,8 +295,12 @@ polylla_status do_traverse(polylla_mesh* h, cudaStream_t s) {
   }));
   const int gp = grid_for(h, M.m, kBlock * 4);
   POLY_TRY(launch(h, "trav_write", s, [&] {
-    return launch_trav_write(M, h->succ, h->P.start, h->P.len, h->off_trav, h->vtx_trav, h->C, gp,
-                             s);
+    return launch_trav_write(M, h->succ, h->P.start, h->P.len, h->P.mode, h->off_trav,
+                             h->vtx_trav, h->C, gp, s);
+  }));
+  const int gl = grid_for(h, 3 * M.m, kBlock * 4);
+  POLY_TRY(launch(h, "long_write", s, [&] {
+    return launch_long_write(M, h->LM, h->P, h->off_trav, h->vtx_trav, 0, h->C, gl, s);
   }));
   h->phase = kTraversed;
   h->latest_csr = 0;
@@ -283,8 +319,13 @@ polylla_status do_repair(polylla_mesh* h, cudaStream_t s, bool copy_from_trav) {
                   [&] { return launch_tip_mark(M, h->lab, h->T, h->epoch, h->C, gtip, s); }));
   POLY_TRY(launch(h, "resucc", s,
                   [&] { return launch_resucc(M, h->lab, h->succ, h->T, h->C, gtip, s); }));
-  POLY_TRY(launch(h, "piece_walk", s,
-                  [&] { return launch_piece_walk(M, h->succ, h->T, h->epoch, h->C, gtip, s); }));
+  POLY_TRY(launch(h, "long_repair", s, [&] {
+    return launch_long_repair(M, h->succ, h->P, h->T, h->Lg, h->LM, h->LM2, h->F, h->loc, h->epoch,
+                              h->C, 2 * h->sms, s);
+  }));
+  POLY_TRY(launch(h, "piece_walk", s, [&] {
+    return launch_piece_walk(M, h->succ, h->P, h->T, h->epoch, h->C, gtip, s);
+  }));
   POLY_TRY(launch(h, "poly_order", s,
                   [&] { return launch_poly_order(M, h->P, h->T, h->F, h->C, gp, s); }));
   POLY_TRY(launch(h, "final_tiles", s,
@@ -303,6 +344,13 @@ polylla_status do_repair(polylla_mesh* h, cudaStream_t s, bool copy_from_trav) {
   }));
   POLY_TRY(launch(h, "final_write_pieces", s, [&] {
     return launch_final_write_pieces(M, h->succ, h->F, h->vtx_final, h->C, gtip, s);
+  }));
+  const int gl = grid_for(h, 3 * M.m, kBlock * 4);
+  POLY_TRY(launch(h, "long_write", s, [&] {
+    return launch_long_write(M, h->LM, h->P, nullptr, h->vtx_final, 1, h->C, gl, s);
+  }));
+  POLY_TRY(launch(h, "long_write_pieces", s, [&] {
+    return launch_long_write_pieces(M, h->LM2, h->T, h->F, h->vtx_final, h->C, gl, s);
   }));
   h->phase = kRepaired;
   h->latest_csr = 1;

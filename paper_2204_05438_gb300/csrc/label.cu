@@ -158,9 +158,12 @@ cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int gr
 // Neighbour label bytes are read while other threads rewrite them; only their
 // bits 0-1 (the Max array, written by the previous kernel) are used, and every
 // rewrite keeps those bits.
+// When tf is given, also writes tf[h] = twin(h) with bit 31 set iff h is frontier
+// (0x7fffffff as the twin of a border half-edge): one load then tells both
+// whether a walk stops at h and where it turns next.
 __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
                                                         long long* __restrict__ tile_sum,
-                                                        Counters* C) {
+                                                        int* __restrict__ tf, Counters* C) {
   __shared__ int sh[kBlock / 32];
   const long long m = M.m;
   const long long H = 3 * m;
@@ -180,6 +183,7 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
         for (int j = 0; t0 + j < m; ++j) own |= (unsigned)lab[t0 + j] << (8 * j);
       }
       unsigned out = 0;
+      int tfo[12];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const long long t = t0 + j;
@@ -201,6 +205,7 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
           }
           const bool fr = (gk < 0) || (k != kst && !((nbm >> k) & 1u));
           byte |= (unsigned)fr << (2 + k);
+          tfo[3 * j + k] = (gk & 0x7fffffff) | (fr ? (int)0x80000000u : 0);
         }
         const int gs = (kst == 0) ? tw[3 * j] : ((kst == 1) ? tw[3 * j + 1] : tw[3 * j + 2]);
         const bool terminal = (gs < 0) || ((nbm >> kst) & 1u);
@@ -212,9 +217,18 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
       }
       if (full) {
         *reinterpret_cast<volatile unsigned*>(lab + t0) = out;
+        if (tf) {
+          int4* q = reinterpret_cast<int4*>(tf) + 3 * g;
+          q[0] = make_int4(tfo[0], tfo[1], tfo[2], tfo[3]);
+          q[1] = make_int4(tfo[4], tfo[5], tfo[6], tfo[7]);
+          q[2] = make_int4(tfo[8], tfo[9], tfo[10], tfo[11]);
+        }
       } else {
-        for (int j = 0; t0 + j < m; ++j)
+        for (int j = 0; t0 + j < m; ++j) {
           *(reinterpret_cast<volatile uint8_t*>(lab) + t0 + j) = (uint8_t)(out >> (8 * j));
+          if (tf)
+            for (int k = 0; k < 3; ++k) tf[3 * (t0 + j) + k] = tfo[3 * j + k];
+        }
       }
     }
     const int tot = block_sum(nseed, sh);
@@ -225,9 +239,9 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
   }
 }
 
-cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, Counters* C,
-                               int grid, cudaStream_t s) {
-  k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tile_sum, C);
+cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, int* tf,
+                               Counters* C, int grid, cudaStream_t s) {
+  k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tile_sum, tf, C);
   return cudaGetLastError();
 }
 

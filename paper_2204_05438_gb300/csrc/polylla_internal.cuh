@@ -32,6 +32,9 @@ struct Counters {
   long long n_vtx;        // final total length
   long long piece_alloc;  // final piece slots handed out
   long long n_pairs;      // (tip -> tip) split-edge pairs found by reparation
+  long long n_long;       // polygons longer than the walk cap
+  long long lm_alloc;     // members of long polygons written
+  long long lm2_alloc;    // members of long polygons' pieces written
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
   int error;              // first device error (polylla_status), 0 if none
@@ -109,8 +112,8 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 cudaError_t launch_validate(const DevMesh& M, Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int grid,
                              cudaStream_t s);
-cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, Counters* C,
-                               int grid, cudaStream_t s);
+cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, int* tf,
+                               Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
                               int* seeds, int grid, cudaStream_t s);
 // Exclusive scan of per-tile pairs.  Tile count = ceil(n / tile) with n = *n_dev if
@@ -130,6 +133,23 @@ struct PolyArrays {
   int* pcnt;      // final pieces
   int* flen;      // total length of the final pieces
   long long* vb;  // output vertex offset
+  int* mode;      // 0 walked by one thread; 1 long (one block); 2 long, generic
+                  // kernels; 3 long with pieces from the block's reparation
+  int* lmbase;    // first entry of a long polygon's members (cycle order)
+};
+
+// Polygons longer than the walk cap (capacity m).
+struct LongList {
+  int* poly;
+  long long cap;
+};
+
+// Members of long polygons (or of their pieces): half-edge, owner, rank.
+struct LongMembers {
+  int* h;
+  int* poly;  // polygon (traversal) or naming record (pieces)
+  int* rank;  // rank in the piece (pieces only)
+  long long cap;
 };
 
 // Barrier-edge tips (capacity = n vertices), grouped by polygon.
@@ -141,6 +161,7 @@ struct TipArrays {
   int* piece;          // [2 per tip] record naming the piece on each side
   int* rec_start;      // [2 per tip] canonical start of the named piece
   int* rec_len;        // [2 per tip] its length
+  int* rec_slot;       // [2 per tip] final piece slot of a naming record
   int* pair_src;       // (tip -> tip) pairs
   int* pair_dst;
   int* cancel_round;
@@ -155,21 +176,37 @@ struct FinalPieces {
   int* start;
   int* len;
   long long* off;
+  int* src;  // 0 written by a walk, 1 from a long polygon's member list
   long long cap;
 };
 
-cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, int* succ, Counters* C, int grid,
+cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
                         cudaStream_t s);
 cudaError_t launch_trav_count(const DevMesh& M, const uint8_t* lab, const int* seeds,
-                              const int* succ, const PolyArrays& P, const TipArrays& T, int epoch,
-                              Counters* C, int grid, cudaStream_t s);
+                              const int* succ, const PolyArrays& P, const TipArrays& T,
+                              const LongList& Lg, int epoch, Counters* C, int grid,
+                              cudaStream_t s);
+cudaError_t launch_long_trav(const DevMesh& M, const int* tf, const int* seeds, const int* succ,
+                             const PolyArrays& P, const TipArrays& T, const LongList& Lg,
+                             const LongMembers& LM, int* visit, int* loc, int epoch, Counters* C,
+                             int grid, cudaStream_t s);
+cudaError_t launch_long_write(const DevMesh& M, const LongMembers& LM, const PolyArrays& P,
+                              const long long* off, int* vtx, int final_pass, Counters* C, int grid,
+                              cudaStream_t s);
+cudaError_t launch_long_repair(const DevMesh& M, const int* succ, const PolyArrays& P,
+                               const TipArrays& T, const LongList& Lg, const LongMembers& LM,
+                               const LongMembers& LM2, const FinalPieces& F, int* loc, int epoch,
+                               Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_long_write_pieces(const DevMesh& M, const LongMembers& LM2, const TipArrays& T,
+                                     const FinalPieces& F, int* vtx, Counters* C, int grid,
+                                     cudaStream_t s);
 cudaError_t launch_len_tiles(const int* len, long long* tile_sum, Counters* C, int grid,
                              cudaStream_t s);
 cudaError_t launch_offsets(const int* len, const long long* tile_off, long long* off, Counters* C,
                            int grid, cudaStream_t s);
 cudaError_t launch_trav_write(const DevMesh& M, const int* succ, const int* start, const int* len,
-                              const long long* off, int* vtx, Counters* C, int grid,
-                              cudaStream_t s);
+                              const int* mode, const long long* off, int* vtx, Counters* C,
+                              int grid, cudaStream_t s);
 cudaError_t launch_tip_split(const DevMesh& M, const uint8_t* lab, const TipArrays& T, int epoch,
                              Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_tip_resolve(const TipArrays& T, Counters* C, cudaStream_t s);
@@ -177,8 +214,9 @@ cudaError_t launch_tip_mark(const DevMesh& M, uint8_t* lab, const TipArrays& T, 
                             Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_resucc(const DevMesh& M, const uint8_t* lab, int* succ, const TipArrays& T,
                           Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_piece_walk(const DevMesh& M, const int* succ, const TipArrays& T, int epoch,
-                              Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_piece_walk(const DevMesh& M, const int* succ, const PolyArrays& P,
+                              const TipArrays& T, int epoch, Counters* C, int grid,
+                              cudaStream_t s);
 cudaError_t launch_poly_order(const DevMesh& M, const PolyArrays& P, const TipArrays& T,
                               const FinalPieces& F, Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_final_tiles(const PolyArrays& P, long long* tile_sum, Counters* C, int grid,

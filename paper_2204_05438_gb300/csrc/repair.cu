@@ -17,7 +17,7 @@
 // (k_piece_walk); their output order is the paper's recursive in-place order
 // (first split at the smallest tip, the half containing tip->x first), rebuilt per
 // polygon from the tree of splits (k_poly_order).
-#include "walk.cuh"
+#include "order.cuh"
 
 namespace polylla {
 
@@ -219,7 +219,8 @@ cudaError_t launch_resucc(const DevMesh& M, const uint8_t* lab, int* succ, const
 // the walker that starts on that half-edge records the piece's canonical start
 // and length.
 __global__ void __launch_bounds__(kBlock) k_piece_walk(DevMesh M, const int* __restrict__ succ,
-                                                       TipArrays T, int epoch, Counters* C) {
+                                                       PolyArrays P, TipArrays T, int epoch,
+                                                       Counters* C) {
   const long long nt = C->n_tips;
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_piece_walk(DevMesh M, const int* __r
        q += (long long)gridDim.x * blockDim.x) {
     const long long k = q >> 1;
     const int oj = T.o[k];
-    if (T.state[k] != 1 || oj < 0) continue;
+    if (T.state[k] != 1 || oj < 0 || P.mode[T.poly[k]] == 3) continue;
     const int h0 = (q & 1) ? M.twin[oj] : oj;
     unsigned long long best = ~0ull;
     int leader = 0x7fffffff, leader_rec = -1;
@@ -263,145 +264,22 @@ __global__ void __launch_bounds__(kBlock) k_piece_walk(DevMesh M, const int* __r
   }
 }
 
-cudaError_t launch_piece_walk(const DevMesh& M, const int* succ, const TipArrays& T, int epoch,
-                              Counters* C, int grid, cudaStream_t s) {
-  k_piece_walk<<<grid, kBlock, 0, s>>>(M, succ, T, epoch, C);
+cudaError_t launch_piece_walk(const DevMesh& M, const int* succ, const PolyArrays& P,
+                              const TipArrays& T, int epoch, Counters* C, int grid,
+                              cudaStream_t s) {
+  k_piece_walk<<<grid, kBlock, 0, s>>>(M, succ, P, T, epoch, C);
   return cudaGetLastError();
 }
 
-// R6: per polygon with tips, order its pieces as the paper's recursion would emit
-// them.  The processed split edges are non-crossing chords of the polygon's disk,
-// so chords and pieces form a tree.  The recursion cuts the chord of the smallest
-// tip first and emits the tip->x side before the other; the same order comes from
-// merging pieces across chords in decreasing tip order (union-find), each merge
-// making a node whose left child holds the tip->x side, and reading the leaves in
-// order.  Scratch: 24 ints per tip of the polygon.
-__device__ void heap_sift(int* key, int* val, int root, int n) {
-  for (;;) {
-    int c = 2 * root + 1;
-    if (c >= n) return;
-    if (c + 1 < n && key[c + 1] > key[c]) ++c;
-    if (key[root] >= key[c]) return;
-    int t = key[root]; key[root] = key[c]; key[c] = t;
-    t = val[root]; val[root] = val[c]; val[c] = t;
-    root = c;
-  }
-}
-
+// R6: per polygon with tips, its pieces in the paper's recursive order
+// (order_pieces, order.cuh); long polygons are ordered by their block.
 __global__ void __launch_bounds__(kBlock) k_poly_order(DevMesh M, PolyArrays P, TipArrays T,
                                                        FinalPieces F, Counters* C) {
   const long long n = C->n_seeds;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int nt = P.ntip[i];
-    if (nt == 0) continue;
-    const long long tb = P.tipbase[i];
-    const int W = 2 * nt + 1;
-    int* chord_k = T.scratch + 24 * tb;  // processed chords (tip entries), then sorted
-    int* chord_b = chord_k + nt;         // their tip vertices (sort keys)
-    int* nodeof = chord_b + nt;          // record offset (q - 2 tb) -> piece node
-    int* node_rec = nodeof + 2 * nt;     // piece node -> its leader record
-    int* uf = node_rec + W;
-    int* left = uf + W;
-    int* right = left + W;
-    int* cnt = right + W;
-    int* pos = cnt + W;  // component -> tree node while merging, then in-order start
-    // 1. processed chords and piece nodes (a piece's node is its leader record)
-    int ns = 0, npieces = 0;
-    for (int j = 0; j < nt; ++j) {
-      const long long k = tb + j;
-      if (T.state[k] != 1 || T.o[k] < 0) continue;
-      chord_k[ns] = (int)k;
-      chord_b[ns] = M.tri[T.o[k]];
-      ++ns;
-    }
-    bool bad = (ns == 0);
-    for (int c = 0; c < ns && !bad; ++c) {
-      for (int side = 0; side < 2; ++side) {
-        const long long q = 2ll * chord_k[c] + side;
-        const long long lead = T.piece[q];
-        if (lead < 2 * tb || lead >= 2 * (tb + nt)) {
-          bad = true;
-          break;
-        }
-        if (lead == q) {
-          if (npieces >= ns + 1) {
-            bad = true;
-            break;
-          }
-          node_rec[npieces] = (int)q;
-          nodeof[q - 2 * tb] = npieces++;
-        }
-      }
-    }
-    if (bad || npieces != ns + 1) {
-      set_error(C, POLYLLA_ERR_LIMIT, 67);
-      P.pcnt[i] = 0;
-      P.flen[i] = 0;
-      continue;
-    }
-    // 2. chords in increasing tip vertex (heapsort), merged from the largest down
-    for (int r = ns / 2 - 1; r >= 0; --r) heap_sift(chord_b, chord_k, r, ns);
-    for (int e = ns - 1; e > 0; --e) {
-      int t = chord_b[0]; chord_b[0] = chord_b[e]; chord_b[e] = t;
-      t = chord_k[0]; chord_k[0] = chord_k[e]; chord_k[e] = t;
-      heap_sift(chord_b, chord_k, 0, e);
-    }
-    for (int v = 0; v < npieces; ++v) {
-      uf[v] = v;
-      pos[v] = v;
-    }
-    int nodes = npieces;
-    for (int c = ns - 1; c >= 0 && !bad; --c) {
-      const long long k = chord_k[c];
-      const int na = nodeof[T.piece[2 * k] - 2 * tb];
-      const int nb = nodeof[T.piece[2 * k + 1] - 2 * tb];
-      int ra = na, rb = nb;
-      while (uf[ra] != ra) ra = uf[ra] = uf[uf[ra]];
-      while (uf[rb] != rb) rb = uf[rb] = uf[uf[rb]];
-      if (ra == rb || nodes >= W) {
-        bad = true;
-        break;
-      }
-      const int u = nodes++;
-      left[u] = pos[ra];
-      right[u] = pos[rb];
-      uf[rb] = ra;
-      pos[ra] = u;
-    }
-    if (bad) {
-      set_error(C, POLYLLA_ERR_LIMIT, 68);
-      P.pcnt[i] = 0;
-      P.flen[i] = 0;
-      continue;
-    }
-    // 3. leaf counts bottom-up, in-order starts top-down (the root is the last node)
-    for (int v = 0; v < npieces; ++v) cnt[v] = 1;
-    for (int u = npieces; u < nodes; ++u) cnt[u] = cnt[left[u]] + cnt[right[u]];
-    pos[nodes - 1] = 0;
-    for (int u = nodes - 1; u >= npieces; --u) {
-      pos[left[u]] = pos[u];
-      pos[right[u]] = pos[u] + cnt[left[u]];
-    }
-    // 4. final piece slots
-    const long long base = (long long)atomicAdd(
-        reinterpret_cast<unsigned long long*>(&C->piece_alloc), (unsigned long long)npieces);
-    if (base + npieces > F.cap) {
-      set_error(C, POLYLLA_ERR_LIMIT, 69);
-      P.pcnt[i] = 0;
-      P.flen[i] = 0;
-      continue;
-    }
-    long long total = 0;
-    for (int v = 0; v < npieces; ++v) {
-      const int rec = node_rec[v];
-      F.start[base + pos[v]] = T.rec_start[rec];
-      F.len[base + pos[v]] = T.rec_len[rec];
-      total += T.rec_len[rec];
-    }
-    P.pbase[i] = (int)base;
-    P.pcnt[i] = npieces;
-    P.flen[i] = (int)total;
+    if (P.ntip[i] == 0 || P.mode[i] == 3) continue;  // mode 3: ordered by k_long_repair
+    order_pieces(M, P, T, F, C, i, T.scratch + 24ll * P.tipbase[i], 0);
   }
 }
 
@@ -501,7 +379,7 @@ __global__ void __launch_bounds__(kBlock) k_final_write_polys(
   const int H = (int)(3 * M.m);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    if (P.ntip[i] != 0) continue;
+    if (P.ntip[i] != 0 || P.mode[i] == 1) continue;  // mode 1: written from member ranks
     const int L = P.len[i];
     const long long vb = P.vb[i];
     if (off_trav) {
@@ -529,6 +407,7 @@ __global__ void __launch_bounds__(kBlock) k_final_write_pieces(DevMesh M, const 
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np;
        q += (long long)gridDim.x * blockDim.x) {
     const int L = F.len[q];
+    if (F.src[q] != 0) continue;  // pieces of long polygons come from their member lists
     if (L > 0 && !succ_write(M.tri, succ, F.start[q], L, H, vtx + F.off[q]))
       set_error(C, POLYLLA_ERR_LIMIT, 72);
   }

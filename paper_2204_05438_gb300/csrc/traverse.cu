@@ -3,11 +3,11 @@
 //   k_succ        one thread per triangle: for each frontier half-edge, the next
 //                 frontier half-edge of its region's boundary (the turn of
 //                 PolyConstruction), with the barrier-edge tip flag.
-//   k_trav_count  one seed per thread (grid-stride, no block barriers, so a long
-//                 walk holds up only its own thread): enter the region, chase succ
-//                 around the cycle, record the canonical start, the length, and
-//                 every barrier-edge tip (appended to the tip list with its
-//                 polygon and its vertex -> tip map entry).
+//   k_trav_count  one seed per thread (grid-stride, no block barriers): enter the
+//                 region, chase succ around the cycle, record the canonical start,
+//                 the length, and every barrier-edge tip (appended to the tip list
+//                 with its polygon and its vertex -> tip map entry).  A cycle
+//                 longer than kWalkCap goes to k_long_trav (long.cu).
 //   k_len_tiles / k_offsets  per-tile length sums, then (after the tile scan) each
 //                 polygon's CSR offset -- the paper's AtomicAdd on i_Gmesh / i_Gpos
 //                 becomes this deterministic scan.
@@ -17,43 +17,70 @@
 
 namespace polylla {
 
-__global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const uint8_t* __restrict__ lab,
+// The three turns of a triangle advance together (independent loads in flight);
+// each step reads one tf word: its sign says frontier, its low bits the twin.
+__global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const int* __restrict__ tf,
                                                  int* __restrict__ succ, Counters* C) {
   const long long m = M.m;
   const int H = (int)(3 * m);
-  const long long limit = 3 * m + 3;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
        t += (long long)gridDim.x * blockDim.x) {
-    const unsigned fr = (__ldg(lab + t) >> 2) & 7u;
-    if (!fr) continue;
+    int x[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k] = __ldg(tf + 3 * t + k);
+    int cur[3], y[3];
+    unsigned active = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      if (!((fr >> k) & 1u)) continue;
-      const int h = (int)(3 * t + k);
-      const int g = turn_to_frontier(M.twin, lab, h, H, limit);
-      if (g < 0) {
-        set_error(C, POLYLLA_ERR_LIMIT, 50);
-        succ[h] = h;  // a one-element cycle keeps later walks bounded
-        continue;
-      }
-      succ[h] = (g == __ldg(M.twin + h)) ? (g | kTipFlag) : g;
+      if (x[k] >= 0) continue;  // not frontier: no successor
+      const int kn = (k == 2) ? 0 : k + 1;
+      cur[k] = (int)(3 * t + kn);
+      y[k] = x[kn];
+      active |= 1u << k;
     }
+    for (long long step = 0; active && step <= 3 * m; ++step) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (!((active >> k) & 1u)) continue;
+        if (y[k] < 0) {  // reached a frontier half-edge
+          const int h = (int)(3 * t + k);
+          const int g = cur[k];
+          succ[h] = (g == (x[k] & 0x7fffffff)) ? (g | kTipFlag) : g;
+          active &= ~(1u << k);
+          continue;
+        }
+        const int tw = y[k];
+        if (tw >= H) {
+          set_error(C, POLYLLA_ERR_LIMIT, 50);
+          succ[3 * t + k] = (int)(3 * t + k);
+          active &= ~(1u << k);
+          continue;
+        }
+        cur[k] = he_next(tw);
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if ((active >> k) & 1u) y[k] = tf[cur[k]];
+    }
+    if (active) set_error(C, POLYLLA_ERR_LIMIT, 50);
   }
 }
 
-cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, int* succ, Counters* C, int grid,
+cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
                         cudaStream_t s) {
-  k_succ<<<grid, kBlock, 0, s>>>(M, lab, succ, C);
+  k_succ<<<grid, kBlock, 0, s>>>(M, tf, succ, C);
   return cudaGetLastError();
 }
 
 constexpr int kLocalTips = 8;
 
+// Walks stop after kWalkCap half-edges: a longer polygon is handed to one block of
+// k_long_trav (mode 1), so that no single thread walks a thousand-vertex cycle.
 __global__ void __launch_bounds__(kBlock) k_trav_count(DevMesh M, const uint8_t* __restrict__ lab,
                                                        const int* __restrict__ seeds,
                                                        const int* __restrict__ succ,
-                                                       PolyArrays P, TipArrays T, int epoch,
-                                                       Counters* C) {
+                                                       PolyArrays P, TipArrays T, LongList Lg,
+                                                       int epoch, Counters* C) {
   const long long n = C->n_seeds;
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
@@ -65,7 +92,18 @@ __global__ void __launch_bounds__(kBlock) k_trav_count(DevMesh M, const uint8_t*
     int tips[kLocalTips];
     CycleInfo c;
     c.ok = false;
-    if (e >= 0) c = succ_cycle(M.tri, succ, e, H, limit, tips, kLocalTips);
+    if (e >= 0) c = succ_cycle(M.tri, succ, e, H, kWalkCap, tips, kLocalTips);
+    if (e >= 0 && !c.ok && c.len >= kWalkCap) {
+      // long polygon: one block of k_long_trav takes it over
+      P.mode[i] = 1;
+      P.len[i] = 0;
+      P.ntip[i] = 0;
+      const long long j = (long long)atomicAdd(
+          reinterpret_cast<unsigned long long*>(&C->n_long), 1ull);
+      if (j < Lg.cap) Lg.poly[j] = (int)i;
+      continue;
+    }
+    P.mode[i] = 0;
     if (!c.ok) {
       set_error(C, POLYLLA_ERR_LIMIT, 51);
       c.start = 3 * s;
@@ -114,9 +152,10 @@ __global__ void __launch_bounds__(kBlock) k_trav_count(DevMesh M, const uint8_t*
 }
 
 cudaError_t launch_trav_count(const DevMesh& M, const uint8_t* lab, const int* seeds,
-                              const int* succ, const PolyArrays& P, const TipArrays& T, int epoch,
-                              Counters* C, int grid, cudaStream_t s) {
-  k_trav_count<<<grid, kBlock, 0, s>>>(M, lab, seeds, succ, P, T, epoch, C);
+                              const int* succ, const PolyArrays& P, const TipArrays& T,
+                              const LongList& Lg, int epoch, Counters* C, int grid,
+                              cudaStream_t s) {
+  k_trav_count<<<grid, kBlock, 0, s>>>(M, lab, seeds, succ, P, T, Lg, epoch, C);
   return cudaGetLastError();
 }
 
@@ -169,12 +208,14 @@ cudaError_t launch_offsets(const int* len, const long long* tile_off, long long*
 __global__ void __launch_bounds__(kBlock) k_trav_write(DevMesh M, const int* __restrict__ succ,
                                                        const int* __restrict__ start,
                                                        const int* __restrict__ len,
+                                                       const int* __restrict__ mode,
                                                        const long long* __restrict__ off,
                                                        int* __restrict__ vtx, Counters* C) {
   const long long n = C->n_seeds;
   const int H = (int)(3 * M.m);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
+    if (mode[i] == 1) continue;  // long polygons are written from their ranks
     const long long pos = off[i];
     const int L = len[i];
     if (pos + L > (long long)H) {
@@ -187,9 +228,9 @@ __global__ void __launch_bounds__(kBlock) k_trav_write(DevMesh M, const int* __r
 }
 
 cudaError_t launch_trav_write(const DevMesh& M, const int* succ, const int* start, const int* len,
-                              const long long* off, int* vtx, Counters* C, int grid,
-                              cudaStream_t s) {
-  k_trav_write<<<grid, kBlock, 0, s>>>(M, succ, start, len, off, vtx, C);
+                              const int* mode, const long long* off, int* vtx, Counters* C,
+                              int grid, cudaStream_t s) {
+  k_trav_write<<<grid, kBlock, 0, s>>>(M, succ, start, len, mode, off, vtx, C);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ namespace polylla {
 
 constexpr int kTipFlag = 1 << 31;
 constexpr int kSuccMask = 0x7fffffff;
+constexpr int kWalkCap = 64;  // longer polygons go to one thread block each (long.cu)
 
 // Next frontier half-edge after h by turning through internal edges, or -1.
 __device__ __forceinline__ int turn_to_frontier(const int* __restrict__ twin, const uint8_t* lab,
@@ -51,6 +52,21 @@ __device__ __forceinline__ int region_entry(const int* __restrict__ twin, const 
     g = he_next(tw);
   }
   return g;
+}
+
+// region_entry on tf words (sign = frontier, low bits = twin).
+__device__ __forceinline__ int region_entry_tf(const int* __restrict__ tf, int t, int H,
+                                               long long limit) {
+  int g = 3 * t;
+  for (int k = 0; k < 3; ++k)
+    if (tf[3 * t + k] < 0) return 3 * t + k;
+  long long steps = 0;
+  for (;;) {
+    const int x = tf[g];
+    if (x < 0) return g;
+    if (x >= H || ++steps > limit) return -1;
+    g = he_next(x);
+  }
 }
 
 // Canonical key of a frontier half-edge: (origin vertex, half-edge id).
