@@ -70,16 +70,26 @@ def hbm_peak():
 def algorithmic_bytes(name: str, s: dict) -> float:
     """Bytes a kernel must move if every element it needs is read or written once
     (n vertices, m triangles, ns seeds, nv0 / nv traversal / final polygon
-    vertices, np final polygons)."""
+    vertices, np final polygons).  The reparation kernels and the long-polygon
+    kernel touch about 1% of the mesh along dependent-load chains: they are
+    latency-bound and carry no byte count."""
     n, m, ns, nv0, nv, npoly = s["n"], s["m"], s["ns"], s["nv0"], s["nv"], s["np"]
     return {
-        "label_max": 12 * m + 16 * n + m,                 # tri, xy, Max byte
-        "label_class": 12 * m + m + m,                    # twin, label byte in / out
-        "seed_write": m + 4 * ns,                         # label byte, seed list
-        "trav_count": 4 * ns + 4 * nv0 + 4 * (3 * m - nv0) + m + 16 * ns,
-        "repair_split": 4 * ns,
-        "final_write": 12 * ns + 4 * nv + 4 * (3 * m - nv) + m + 8 * (npoly + 1) + 4 * nv,
-        "trav_write": 8 * ns + 4 * nv0 + 4 * (3 * m - nv0) + m + 8 * (ns + 1) + 4 * nv0,
+        # tri (3 x int32) and each vertex's xy (2 x int64) in, one label byte out
+        "label_max": 12 * m + 16 * n + m,
+        # twin in, own and neighbour label bytes in, label byte and tf words out
+        "label_class": 12 * m + 2 * m + 12 * m,
+        # label byte in, seed list out
+        "seed_write": m + 4 * ns,
+        # every tf word once, the successor of every frontier half-edge out
+        "succ": 12 * m + 4 * nv0,
+        # seed and its triangle's tf words, per vertex succ + origin in and pool out,
+        # per polygon its record (start, len, tips, tip, mode, count, length, pos)
+        "walk": 16 * ns + 12 * nv0 + 36 * ns,
+        # per polygon its piece count and length
+        "out_tiles": 8 * ns,
+        # per polygon record in, pool in, offsets and vertices out
+        "out_write": 16 * ns + 8 * nv + 8 * (npoly + 1),
     }.get(name, 0.0)
 
 
@@ -242,6 +252,8 @@ def run_ours(args, dist: Dist) -> dict | None:
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["gbs"], "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
                 "traffic": traffic, "alg_bytes_per_launch": kernels[dom]["alg_bytes"]}
+    step_bytes = sum(k["alg_bytes"] for k in kernels.values())
+    step_gbs = step_bytes / (ms_per_step * 1e-3) / 1e9
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
@@ -283,6 +295,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         "label_seed": {"ms": round(ls_ms, 5), "alg_bytes": int(ls_bytes),
                        "gbs": round(ls_bytes / (ls_ms * 1e-3) / 1e9, 1) if ls_ms else None,
                        "frac": round(ls_bytes / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None},
+        "step_roofline": {"alg_bytes": int(step_bytes), "gbs": round(step_gbs, 1),
+                          "frac": round(step_gbs / peak, 4)},
         "kernels": kernels,
         "mesh_stats": st,
         "e2e": e2e,

@@ -7,6 +7,7 @@
 // host; phases only enqueue kernels on the caller's stream.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -38,16 +39,17 @@ struct polylla_mesh {
 
   uint8_t* lab = nullptr;
   int* seeds = nullptr;
-  int* succ = nullptr;
+  int* succ = nullptr;    // boundary successor of every frontier half-edge
   int* tf = nullptr;      // twin | frontier bit, per half-edge (written by the label phase)
-  int* visit = nullptr;   // per triangle: BFS stamp of the long-polygon blocks
+  int* visit = nullptr;   // per triangle: search stamp of the long-polygon blocks
   int* loc = nullptr;     // per half-edge: member index inside a long-polygon block
+  int* vstamp = nullptr;  // per vertex: "endpoint of a split edge" stamp
   LongList Lg{};
-  LongMembers LM{};
-  LongMembers LM2{};
+  LongList Dl{};          // polygons with one tip
   PolyArrays P{};
-  TipArrays T{};
   FinalPieces F{};
+  Pool pool{};
+  LongList Dm{};          // polygons with several tips
   int epoch = 0;
   long long* tile_sum = nullptr;
   long long* tile_off = nullptr;
@@ -121,16 +123,13 @@ cudaError_t dalloc(T** p, long long count) {
 }
 
 void free_all(polylla_mesh* h) {
-  void* ptrs[] = {h->lab,         h->seeds,        h->succ,         h->P.start,     h->P.len,
-                  h->P.ntip,      h->P.tipbase,    h->P.pbase,      h->P.pcnt,      h->P.flen,
-                  h->P.vb,        h->T.h,          h->T.poly,       h->T.o,         h->T.state,
-                  h->T.piece,     h->T.rec_start,  h->T.rec_len,    h->T.pair_src,  h->T.pair_dst,
-                  h->T.cancel_round, h->T.scratch, h->T.vtip,       h->T.chord,     h->F.start,
-                  h->F.len,       h->F.off,        h->tile_sum,     h->tile_off,    h->off_trav,
-                  h->vtx_trav,    h->off_final,    h->vtx_final,    h->C,           h->tf,
-                  h->visit,       h->loc,          h->Lg.poly,      h->LM.h,        h->LM.poly,
-                  h->LM2.h,       h->LM2.poly,     h->LM2.rank,     h->P.mode,      h->P.lmbase,
-                  h->F.src,       h->T.rec_slot};
+  void* ptrs[] = {h->lab,      h->seeds,     h->succ,      h->tf,         h->visit,
+                  h->loc,      h->vstamp,    h->Lg.poly,   h->P.start,    h->P.len,
+                  h->P.ntip,   h->P.mode,    h->P.pcnt,    h->P.pbase,    h->P.flen,
+                  h->P.pos,    h->F.pos,     h->F.len,     h->F.h,        h->pool.v,
+                  h->tile_sum, h->tile_off,  h->off_trav,  h->vtx_trav,   h->off_final,
+                  h->vtx_final, h->C,         h->Dl.poly,   h->P.tip_h,
+                  h->Dm.poly};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_inputs) {
@@ -150,38 +149,40 @@ polylla_status alloc_derived(polylla_mesh* h) {
   const long long ntiles_tri = (m + kTriTile - 1) / kTriTile;
   const long long ntiles_poly = (m + kPolyTile - 1) / kPolyTile;
   const long long ntiles = ntiles_tri > ntiles_poly ? ntiles_tri : ntiles_poly;
-  h->T.cap = n;       // a vertex is the tip of at most one barrier edge
-  h->F.cap = m + 1;   // final polygons <= m
+  // bounds: at most m polygons and 3m polygon vertices after reparation; the pool
+  // also holds the up to 2 extra slots per tip a splitting thread reserves, and
+  // there is at most one piece record per tip plus one per polygon
+  h->Lg.cap = m;
+  h->Dl.cap = m;
+  h->F.cap = n + m;
+  h->pool.cap = 6 * m + 2 * n;
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, cnt) \
   if (e == cudaSuccess) e = dalloc(&(ptr), (cnt))
   ALLOC(h->lab, m + 4);
   ALLOC(h->seeds, m);
   ALLOC(h->succ, 3 * m);
+  ALLOC(h->tf, 3 * m);
+  ALLOC(h->visit, m);
+  ALLOC(h->loc, 3 * m);
+  ALLOC(h->vstamp, n);
+  ALLOC(h->Lg.poly, m);
+  ALLOC(h->Dl.poly, m);
+  ALLOC(h->P.tip_h, m);
+  h->Dm.cap = m;
+  ALLOC(h->Dm.poly, m);
   ALLOC(h->P.start, m);
   ALLOC(h->P.len, m);
   ALLOC(h->P.ntip, m);
-  ALLOC(h->P.tipbase, m);
-  ALLOC(h->P.pbase, m);
+  ALLOC(h->P.mode, m);
   ALLOC(h->P.pcnt, m);
+  ALLOC(h->P.pbase, m);
   ALLOC(h->P.flen, m);
-  ALLOC(h->P.vb, m);
-  ALLOC(h->T.h, n);
-  ALLOC(h->T.poly, n);
-  ALLOC(h->T.o, n);
-  ALLOC(h->T.state, n);
-  ALLOC(h->T.piece, 2 * n);
-  ALLOC(h->T.rec_start, 2 * n);
-  ALLOC(h->T.rec_len, 2 * n);
-  ALLOC(h->T.pair_src, n);
-  ALLOC(h->T.pair_dst, n);
-  ALLOC(h->T.cancel_round, n);
-  ALLOC(h->T.scratch, 24 * n);
-  ALLOC(h->T.vtip, n);
-  ALLOC(h->T.chord, 3 * m);
-  ALLOC(h->F.start, h->F.cap);
+  ALLOC(h->P.pos, m);
+  ALLOC(h->F.pos, h->F.cap);
   ALLOC(h->F.len, h->F.cap);
-  ALLOC(h->F.off, h->F.cap);
+  ALLOC(h->F.h, h->F.cap);
+  ALLOC(h->pool.v, h->pool.cap);
   ALLOC(h->tile_sum, 2 * ntiles);
   ALLOC(h->tile_off, 2 * ntiles);
   ALLOC(h->off_trav, m + 1);
@@ -189,27 +190,10 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->off_final, m + 1);
   ALLOC(h->vtx_final, 3 * m);
   ALLOC(h->C, 1);
-  ALLOC(h->tf, 3 * m);
-  ALLOC(h->visit, m);
-  ALLOC(h->loc, 3 * m);
-  ALLOC(h->Lg.poly, m);
-  ALLOC(h->LM.h, 3 * m);
-  ALLOC(h->LM.poly, 3 * m);
-  ALLOC(h->LM2.h, 3 * m);
-  ALLOC(h->LM2.poly, 3 * m);
-  ALLOC(h->LM2.rank, 3 * m);
-  ALLOC(h->P.mode, m);
-  ALLOC(h->P.lmbase, m);
-  ALLOC(h->F.src, h->F.cap);
-  ALLOC(h->T.rec_slot, 2 * n);
 #undef ALLOC
-  h->Lg.cap = m;
-  h->LM.cap = 3 * m;
-  h->LM2.cap = 3 * m;
+  // stamped arrays start empty (run stamps are never 0)
   if (e == cudaSuccess) e = cudaMemset(h->visit, 0, sizeof(int) * (size_t)m);
-  // epoch-tagged maps start empty (epochs start at 1)
-  if (e == cudaSuccess) e = cudaMemset(h->T.vtip, 0, sizeof(long long) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMemset(h->T.chord, 0, sizeof(long long) * (size_t)(3 * m));
+  if (e == cudaSuccess) e = cudaMemset(h->vstamp, 0, sizeof(int) * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(h->C, 0, sizeof(Counters));
   return cuda_status(e);
 }
@@ -233,10 +217,9 @@ polylla_status check_handle(polylla_mesh* h) {
 // ---------------------------------------------------------------- phases
 polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   const DevMesh& M = h->M;
-  if (h->epoch >= 0x7ffffff0) {  // epoch-tagged maps: wrap around once in 2^31 runs
-    POLY_TRY(cuda_status(cudaMemsetAsync(h->T.vtip, 0, sizeof(long long) * (size_t)M.n, s)));
-    POLY_TRY(cuda_status(cudaMemsetAsync(h->T.chord, 0, sizeof(long long) * (size_t)(3 * M.m), s)));
+  if (h->epoch >= 0x3ffffff0) {  // stamps: wrap around once in 2^30 runs
     POLY_TRY(cuda_status(cudaMemsetAsync(h->visit, 0, sizeof(int) * (size_t)M.m, s)));
+    POLY_TRY(cuda_status(cudaMemsetAsync(h->vstamp, 0, sizeof(int) * (size_t)M.n, s)));
     h->epoch = 0;
   }
   ++h->epoch;
@@ -244,8 +227,9 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   const int g1 = grid_for(h, (M.m + 3) / 4, kBlock);
   POLY_TRY(launch(h, "label_max", s, [&] { return launch_label_max(M, h->lab, h->C, g1, s); }));
   const int g2 = grid_for(h, M.m, kTriTile);
-  POLY_TRY(launch(h, "label_class", s,
-                  [&] { return launch_label_class(M, h->lab, h->tile_sum, h->tf, h->C, g2, s); }));
+  POLY_TRY(launch(h, "label_class", s, [&] {
+    return launch_label_class(M, h->lab, h->tile_sum, h->tf, h->C, g2, s);
+  }));
   h->phase = kLabeled;
   h->latest_csr = -1;
   return POLYLLA_OK;
@@ -264,94 +248,58 @@ polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
   return POLYLLA_OK;
 }
 
-// successor of every frontier half-edge, then one walk per seed
-polylla_status do_trav_count(polylla_mesh* h, cudaStream_t s) {
+// Walk every polygon (one thread, or one block for a long one) into the pool,
+// splitting those with tips when `repair`; then the CSR.
+polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long long* off, int* vtx) {
   const DevMesh& M = h->M;
-  const int gt = grid_for(h, M.m, kBlock);
-  POLY_TRY(launch(h, "succ", s, [&] { return launch_succ(M, h->tf, h->succ, h->C, gt, s); }));
-  const int gp = grid_for(h, M.m, kBlock * 4);
-  POLY_TRY(launch(h, "trav_count", s, [&] {
-    return launch_trav_count(M, h->lab, h->seeds, h->succ, h->P, h->T, h->Lg, h->epoch, h->C, gp,
-                             s);
+  // counters of this pass start at zero (the traversal pass may have run before)
+  const size_t first = offsetof(Counters, n_vtx_trav);
+  const size_t last = offsetof(Counters, scratch0);
+  POLY_TRY(cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(h->C) + first, 0, last - first, s)));
+  if (repair == 0 || h->phase < kTraversed) {
+    const int gt = grid_for(h, M.m, kBlock);
+    POLY_TRY(launch(h, "succ", s, [&] { return launch_succ(M, h->tf, h->succ, h->C, gt, s); }));
+  }
+  const int gw = grid_for(h, M.m, 4 * 256);
+  POLY_TRY(launch(h, "walk", s, [&] {
+    return launch_walk(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg, h->Dl,
+                       h->Dm, repair, h->C, gw, s);
   }));
-  return launch(h, "long_trav", s, [&] {
-    return launch_long_trav(M, h->tf, h->seeds, h->succ, h->P, h->T, h->Lg, h->LM, h->visit,
-                            h->loc, h->epoch, h->C, 2 * h->sms, s);
+  if (repair) {
+    POLY_TRY(launch(h, "repair_one", s, [&] {
+      return launch_repair_one(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dl, h->C,
+                               h->sms, s);
+    }));
+    POLY_TRY(launch(h, "repair_multi", s, [&] {
+      return launch_repair_multi(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dm, h->C,
+                                 h->sms, s);
+    }));
+  }
+  POLY_TRY(launch(h, "long", s, [&] {
+    return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg, h->visit,
+                       h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->C, 2 * h->sms, s);
+  }));
+  const int gt = grid_for(h, M.m, kPolyTile);
+  POLY_TRY(launch(h, "out_tiles", s,
+                  [&] { return launch_final_tiles(h->P, h->tile_sum, h->C, gt, s); }));
+  POLY_TRY(launch(h, "out_scan", s, [&] {
+    return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
+                             &h->C->n_poly, &h->C->n_vtx, off, 2, M.m, h->C, s);
+  }));
+  return launch(h, "out_write", s, [&] {
+    return launch_final_write(h->P, h->F, h->pool, h->tile_off, off, vtx, M.m, h->C, gt, s);
   });
 }
 
 polylla_status do_traverse(polylla_mesh* h, cudaStream_t s) {
-  const DevMesh& M = h->M;
-  POLY_TRY(do_trav_count(h, s));
-  const int gt = grid_for(h, M.m, kPolyTile);
-  POLY_TRY(launch(h, "len_tiles", s,
-                  [&] { return launch_len_tiles(h->P.len, h->tile_sum, h->C, gt, s); }));
-  POLY_TRY(launch(h, "scan_trav", s, [&] {
-    return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
-                             &h->C->scratch0, &h->C->scratch1, h->off_trav, 1, M.m, h->C, s);
-  }));
-  POLY_TRY(launch(h, "trav_offsets", s, [&] {
-    return launch_offsets(h->P.len, h->tile_off, h->off_trav, h->C, gt, s);
-  }));
-  const int gp = grid_for(h, M.m, kBlock * 4);
-  POLY_TRY(launch(h, "trav_write", s, [&] {
-    return launch_trav_write(M, h->succ, h->P.start, h->P.len, h->P.mode, h->off_trav,
-                             h->vtx_trav, h->C, gp, s);
-  }));
-  const int gl = grid_for(h, 3 * M.m, kBlock * 4);
-  POLY_TRY(launch(h, "long_write", s, [&] {
-    return launch_long_write(M, h->LM, h->P, h->off_trav, h->vtx_trav, 0, h->C, gl, s);
-  }));
+  POLY_TRY(do_polygons(h, s, 0, h->off_trav, h->vtx_trav));
   h->phase = kTraversed;
   h->latest_csr = 0;
   return POLYLLA_OK;
 }
 
-polylla_status do_repair(polylla_mesh* h, cudaStream_t s, bool copy_from_trav) {
-  const DevMesh& M = h->M;
-  const int gtip = grid_for(h, M.n, kBlock * 4);
-  const int gp = grid_for(h, M.m, kBlock * 4);
-  const int gt = grid_for(h, M.m, kPolyTile);
-  POLY_TRY(launch(h, "tip_split", s,
-                  [&] { return launch_tip_split(M, h->lab, h->T, h->epoch, h->C, gtip, s); }));
-  POLY_TRY(launch(h, "tip_resolve", s, [&] { return launch_tip_resolve(h->T, h->C, s); }));
-  POLY_TRY(launch(h, "tip_mark", s,
-                  [&] { return launch_tip_mark(M, h->lab, h->T, h->epoch, h->C, gtip, s); }));
-  POLY_TRY(launch(h, "resucc", s,
-                  [&] { return launch_resucc(M, h->lab, h->succ, h->T, h->C, gtip, s); }));
-  POLY_TRY(launch(h, "long_repair", s, [&] {
-    return launch_long_repair(M, h->succ, h->P, h->T, h->Lg, h->LM, h->LM2, h->F, h->loc, h->epoch,
-                              h->C, 2 * h->sms, s);
-  }));
-  POLY_TRY(launch(h, "piece_walk", s, [&] {
-    return launch_piece_walk(M, h->succ, h->P, h->T, h->epoch, h->C, gtip, s);
-  }));
-  POLY_TRY(launch(h, "poly_order", s,
-                  [&] { return launch_poly_order(M, h->P, h->T, h->F, h->C, gp, s); }));
-  POLY_TRY(launch(h, "final_tiles", s,
-                  [&] { return launch_final_tiles(h->P, h->tile_sum, h->C, gt, s); }));
-  POLY_TRY(launch(h, "scan_final", s, [&] {
-    return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
-                             &h->C->n_poly, &h->C->n_vtx, h->off_final, 2, M.m, h->C, s);
-  }));
-  POLY_TRY(launch(h, "final_offsets", s, [&] {
-    return launch_final_offsets(h->P, h->F, h->tile_off, h->off_final, M.m, h->C, gt, s);
-  }));
-  POLY_TRY(launch(h, "final_write_polys", s, [&] {
-    return launch_final_write_polys(M, h->succ, h->P, copy_from_trav ? h->off_trav : nullptr,
-                                    copy_from_trav ? h->vtx_trav : nullptr, h->vtx_final, h->C,
-                                    gp, s);
-  }));
-  POLY_TRY(launch(h, "final_write_pieces", s, [&] {
-    return launch_final_write_pieces(M, h->succ, h->F, h->vtx_final, h->C, gtip, s);
-  }));
-  const int gl = grid_for(h, 3 * M.m, kBlock * 4);
-  POLY_TRY(launch(h, "long_write", s, [&] {
-    return launch_long_write(M, h->LM, h->P, nullptr, h->vtx_final, 1, h->C, gl, s);
-  }));
-  POLY_TRY(launch(h, "long_write_pieces", s, [&] {
-    return launch_long_write_pieces(M, h->LM2, h->T, h->F, h->vtx_final, h->C, gl, s);
-  }));
+polylla_status do_repair(polylla_mesh* h, cudaStream_t s) {
+  POLY_TRY(do_polygons(h, s, 1, h->off_final, h->vtx_final));
   h->phase = kRepaired;
   h->latest_csr = 1;
   return POLYLLA_OK;
@@ -470,7 +418,7 @@ polylla_status polylla_repair(polylla_mesh_t h, void* stream) {
   POLY_TRY(check_handle(h));
   if (h->phase != kTraversed) return POLYLLA_ERR_STATE;
   h->last_stream = (cudaStream_t)stream;
-  return do_repair(h, (cudaStream_t)stream, true);
+  return do_repair(h, (cudaStream_t)stream);
 }
 
 polylla_status polylla_run(polylla_mesh_t h, void* stream) {
@@ -479,8 +427,7 @@ polylla_status polylla_run(polylla_mesh_t h, void* stream) {
   h->last_stream = s;
   POLY_TRY(do_label(h, s));
   POLY_TRY(do_seeds(h, s));
-  POLY_TRY(do_trav_count(h, s));
-  return do_repair(h, s, false);
+  return do_repair(h, s);
 }
 
 polylla_status polylla_get_labels(polylla_mesh_t h, const uint8_t** d_lab) {

@@ -1,38 +1,40 @@
 // Long polygons: one thread block per polygon whose boundary has more than
 // kWalkCap vertices.  A handful of regions per mesh are that large (on a
 // 20M-triangle Gaussian-mixture mesh the largest polygon has over a thousand
-// vertices); walking them one dependent load at a time would make each of them the
-// critical path of its phase.  A block instead
+// vertices and almost a hundred tips); walking or splitting them one dependent
+// load at a time would make each of them the critical path of the run.  A block:
 //
-//   * collects the region's frontier half-edges by a breadth-first search over
-//     its triangles across non-frontier edges (tf words).  Every triangle reaches
-//     its seed through its longest-edge links, so the search from the seed ends
-//     after at most (longest-edge propagation depth + 1) levels;
-//   * maps each half-edge's successor to a member index, finds the canonical start
-//     (smallest (origin, id)) by a block reduction, and ranks the cycle from it by
-//     pointer jumping (Wyllie) in shared memory: log2(length) rounds;
-//   * writes the members in cycle order to a compact list, which k_long_write
-//     scatters into the CSR once the offsets are known.
+//   1. collects the region's frontier half-edges by a breadth-first search over
+//      its triangles across non-frontier edges (tf words).  Every triangle reaches
+//      its seed through its longest-edge links, so the search from the seed ends
+//      after at most (longest-edge propagation depth + 1) levels;
+//   2. maps each half-edge's successor to a member index, finds the canonical
+//      start by a block reduction;
+//   3. without reparation (or tips): ranks the cycle from its start by pointer
+//      jumping in shared memory (log2(length) rounds) and writes the members in
+//      cycle order to the pool;
+//   4. with reparation: computes every tip's split edge in parallel, settles in
+//      increasing tip order which tips are removed by a smaller tip's split edge
+//      ending on them (the result of the paper's rounds with the smallest tip
+//      first), marks the split edges frontier, recomputes the successors that end
+//      at their endpoints, finds the pieces as the cycles of the new successor
+//      function (pointer jumping to each cycle's smallest key, which is the piece's
+//      canonical start; a piece is named by its smallest split half-edge), ranks
+//      them, orders them as the recursive splitting emits them (first the chord of
+//      the smallest tip, the tip->x side first: merging pieces across chords in
+//      decreasing tip order builds that tree) and writes them to the pool.
 //
-// k_long_repair does the reparation of a long polygon with tips in the same way:
-// after the split edges are marked and the successors around them recomputed, the
-// members (old frontier half-edges plus the split half-edges) fall into the pieces'
-// cycles; pointer jumping labels every member with its cycle's smallest key (the
-// piece's canonical start), the split half-edge that names the piece, and its rank;
-// the pieces are then ordered as the recursive splitting emits them (the same
-// chord-tree construction as k_poly_order).  A polygon that does not fit the shared
-// memory budget falls back to the generic kernels (mode 2).
-#include "order.cuh"
+// A region too large for the shared-memory budget is handled by one thread of the
+// block with the sequential code (mode 2).
+#include "walk.cuh"
 
 namespace polylla {
 
 constexpr int kLongThreads = 512;
-constexpr int kLongMaxMembers = 6144;  // frontier half-edges of one long polygon
-constexpr int kLongMaxTri = 4096;      // BFS queue (triangles of one long region)
+constexpr int kLM = 4096;  // members of one long polygon (with its split half-edges)
+constexpr int kLT = 4096;  // BFS queue: triangles of one long region
+constexpr int kLongSmemInts = kLT + 10 * kLM;
 
-__device__ __forceinline__ int tf_twin(int x) { return x & 0x7fffffff; }
-
-// Block-wide min of a 64-bit key (with the index that holds it).
 __device__ void block_min_key(unsigned long long key, int idx, unsigned long long* s_key,
                               int* s_idx, unsigned long long* out_key, int* out_idx) {
 #pragma unroll
@@ -73,9 +75,8 @@ __device__ void block_min_key(unsigned long long key, int idx, unsigned long lon
   __syncthreads();
 }
 
-// Pointer jumping on a functional graph given by nx[] (each node's successor;
-// -1 ends a list): after the call, d[i] = number of hops from i to the end of
-// its list.  Buffers a/b are swapped in place; returns the buffer holding d.
+// Pointer jumping on successor lists (nx: successor, or -1 at a list's end):
+// returns the buffer holding, for every node, its number of hops to the end.
 __device__ int* list_rank(int* nx0, int* nx1, int* d0, int* d1, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) d0[i] = (nx0[i] < 0) ? 0 : 1;
   __syncthreads();
@@ -99,64 +100,146 @@ __device__ int* list_rank(int* nx0, int* nx1, int* d0, int* d1, int n) {
   return d0;
 }
 
-// ---------------------------------------------------------------- traversal
-__global__ void __launch_bounds__(kLongThreads) k_long_trav(DevMesh M, const int* __restrict__ tf,
-                                                            const int* __restrict__ seeds,
-                                                            const int* __restrict__ succ,
-                                                            PolyArrays P, TipArrays T, LongList Lg,
-                                                            LongMembers LM, int* __restrict__ visit,
-                                                            int* __restrict__ loc, int epoch,
-                                                            Counters* C) {
+__device__ __forceinline__ void heap_sift(int* key, int* val, int root, int n) {
+  for (;;) {
+    int c = 2 * root + 1;
+    if (c >= n) return;
+    if (c + 1 < n && key[c + 1] > key[c]) ++c;
+    if (key[root] >= key[c]) return;
+    int t = key[root]; key[root] = key[c]; key[c] = t;
+    t = val[root]; val[root] = val[c]; val[c] = t;
+    root = c;
+  }
+}
+
+__device__ void heap_sort(int* key, int* val, int n) {
+  for (int r = n / 2 - 1; r >= 0; --r) heap_sift(key, val, r, n);
+  for (int e = n - 1; e > 0; --e) {
+    int t = key[0]; key[0] = key[e]; key[e] = t;
+    t = val[0]; val[0] = val[e]; val[e] = t;
+    heap_sift(key, val, 0, e);
+  }
+}
+
+// One thread: the sequential path for a region too large for shared memory.
+__device__ void long_fallback(const DevMesh& M, uint8_t* lab, int* tf, int t0, long long i,
+                              PolyArrays& P, FinalPieces& F, Pool& pool, int repair, Counters* C) {
+  const int H = (int)(3 * M.m);
+  const long long limit = 3 * M.m + 3;
+  P.mode[i] = 2;
+  P.pcnt[i] = 0;
+  P.flen[i] = 0;
+  const int e = region_entry_tf(tf, t0, H, limit);
+  if (e < 0) {
+    set_error(C, POLYLLA_ERR_LIMIT, 100);
+    return;
+  }
+  const Cyc c = cycle_tf(M.tri, tf, e, H, limit);
+  if (!c.ok) {
+    set_error(C, POLYLLA_ERR_LIMIT, 101);
+    return;
+  }
+  P.start[i] = c.start;
+  P.len[i] = c.len;
+  P.ntip[i] = c.ntips;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_vtx_trav), (unsigned long long)c.len);
+  if (c.ntips) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_tips), (unsigned long long)c.ntips);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_tip_polys), 1ull);
+  }
+  const bool split = repair && c.ntips > 0;
+  const int need = split ? c.len + 2 * c.ntips : c.len;
+  const long long off = (long long)atomicAdd(
+      reinterpret_cast<unsigned long long*>(&C->pool_alloc), (unsigned long long)need);
+  if (off + need > pool.cap) {
+    set_error(C, POLYLLA_ERR_LIMIT, 102);
+    return;
+  }
+  if (!split) {
+    if (!write_tf(M.tri, tf, c.start, c.len, H, limit, pool.v + off))
+      set_error(C, POLYLLA_ERR_LIMIT, 103);
+    P.pos[i] = off;
+    P.flen[i] = c.len;
+    return;
+  }
+  const long long foff = (long long)atomicAdd(
+      reinterpret_cast<unsigned long long*>(&C->fslot_alloc), (unsigned long long)(c.ntips + 1));
+  if (foff + c.ntips + 1 > F.cap) {
+    set_error(C, POLYLLA_ERR_LIMIT, 104);
+    return;
+  }
+  const int cnt = repair_seq(M.tri, tf, lab, c, c.ntips + 1, H, limit, F.h + foff, F.pos + foff,
+                             F.len + foff, pool.v + off, off);
+  if (cnt < 0) {
+    set_error(C, POLYLLA_ERR_LIMIT, 105);
+    return;
+  }
+  P.pcnt[i] = cnt;
+  P.pbase[i] = (int)foff;
+  P.flen[i] = c.len + 2 * (cnt - 1);
+  atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)(cnt - 1));
+}
+
+__global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* lab, int* tf,
+                                                       const int* __restrict__ seeds,
+                                                       const int* __restrict__ succ, PolyArrays P,
+                                                       FinalPieces F, Pool pool, LongList Lg,
+                                                       int* __restrict__ visit,
+                                                       int* __restrict__ loc,
+                                                       int* __restrict__ vstamp, int epoch,
+                                                       int repair, Counters* C) {
   extern __shared__ int smem[];
-  int* tq = smem;                       // kLongMaxTri
-  int* mem = tq + kLongMaxTri;          // kLongMaxMembers
-  int* nx0 = mem + kLongMaxMembers;
-  int* nx1 = nx0 + kLongMaxMembers;
-  int* d0 = nx1 + kLongMaxMembers;
-  int* d1 = d0 + kLongMaxMembers;
-  __shared__ int s_head, s_tail, s_nm, s_over, s_ntip, s_tipcur;
+  int* RQ = smem;       // BFS queue; later the chord list and ordering counts
+  int* mem = RQ + kLT;  // members
+  int* const R0 = mem + 1 * kLM;
+  int* const R1 = mem + 2 * kLM;
+  int* const R2 = mem + 3 * kLM;
+  int* const R3 = mem + 4 * kLM;
+  int* const R4 = mem + 5 * kLM;
+  int* const R5 = mem + 6 * kLM;
+  int* const R6 = mem + 7 * kLM;
+  int* const R7 = mem + 8 * kLM;
+  int* const R8 = mem + 9 * kLM;
+  __shared__ int s_head, s_tail, s_nm, s_over, s_nt, s_ns, s_fail;
   __shared__ unsigned long long s_key[32];
   __shared__ int s_idx[32];
-  __shared__ long long s_base;
+  __shared__ long long s_base, s_fbase;
   const int H = (int)(3 * M.m);
-  const int stamp = 2 * epoch;
+  const long long limit = 3 * M.m + 3;
   const long long nl = min(C->n_long, Lg.cap);
   for (long long j = blockIdx.x; j < nl; j += gridDim.x) {
-    const int i = Lg.poly[j];
+    const long long i = Lg.poly[j];
     const int t0 = seeds[i];
-    // 1. breadth-first search of the region
+    // ---- 1. breadth-first search of the region
     if (threadIdx.x == 0) {
       s_head = 0;
       s_tail = 1;
       s_nm = 0;
       s_over = 0;
-      tq[0] = t0;
-      visit[t0] = stamp;
+      RQ[0] = t0;
+      visit[t0] = epoch;
     }
     __syncthreads();
     for (;;) {
-      const int lo = s_head, hi = s_tail;
-      const int over = s_over;
+      const int lo = s_head, hi = s_tail, over = s_over;
       __syncthreads();
       if (lo >= hi || over) break;
       for (int q = lo + threadIdx.x; q < hi; q += blockDim.x) {
-        const int t = tq[q];
+        const int t = RQ[q];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int x = tf[3 * t + k];
           if (x < 0) {
             const int mi = atomicAdd(&s_nm, 1);
-            if (mi < kLongMaxMembers) mem[mi] = 3 * t + k;
+            if (mi < kLM) mem[mi] = 3 * t + k;
             else s_over = 1;
+          } else if (x >= H) {
+            s_over = 2;
           } else {
-            if (x >= H) {
-              s_over = 2;
-              continue;
-            }
             const int nb = x / 3;
-            if (atomicExch(visit + nb, stamp) != stamp) {
+            if (atomicExch(visit + nb, epoch) != epoch) {
               const int p = atomicAdd(&s_tail, 1);
-              if (p < kLongMaxTri) tq[p] = nb;
+              if (p < kLT) RQ[p] = nb;
               else s_over = 1;
             }
           }
@@ -168,350 +251,332 @@ __global__ void __launch_bounds__(kLongThreads) k_long_trav(DevMesh M, const int
     }
     const int L = s_nm;
     if (s_over) {
-      // too large for the shared-memory path: the generic walk takes it (mode 2)
       if (threadIdx.x == 0) {
-        if (s_over == 2) set_error(C, POLYLLA_ERR_LIMIT, 100);
-        P.mode[i] = 2;
-        const long long limit = 3 * M.m + 3;
-        const int e = region_entry_tf(tf, t0, H, limit);
-        int len = 0, ntip = 0;
-        unsigned long long best = ~0ull;
-        int h = e;
-        bool ok = e >= 0;
-        while (ok) {
-          const unsigned long long key = he_key(M.tri, h);
-          if (key < best) best = key;
-          const int sg = succ[h];
-          ntip += (sg & kTipFlag) ? 1 : 0;
-          ++len;
-          h = sg & kSuccMask;
-          if ((unsigned)h >= (unsigned)H || len > limit) ok = false;
-          else if (h == e) break;
-        }
-        if (!ok) {
-          set_error(C, POLYLLA_ERR_LIMIT, 101);
-          len = 0;
-          ntip = 0;
-        }
-        P.start[i] = (int)(best & 0xffffffffu);
-        P.len[i] = len;
-        P.ntip[i] = ntip;
-        if (ntip > 0) {
-          const long long base = (long long)atomicAdd(
-              reinterpret_cast<unsigned long long*>(&C->n_tips), (unsigned long long)ntip);
-          P.tipbase[i] = (int)base;
-          int q = 0;
-          h = e;
-          for (int step = 0; step < len && base + q < T.cap; ++step) {
-            const int sg = succ[h];
-            if (sg & kTipFlag) {
-              T.h[base + q] = h;
-              T.poly[base + q] = i;
-              T.vtip[M.tri[he_next(h)]] = ((long long)epoch << 32) | (unsigned)(base + q);
-              ++q;
-            }
-            h = sg & kSuccMask;
-          }
-        }
-        atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_vtx_trav), (unsigned long long)len);
-        if (ntip) atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_tip_polys), 1ull);
+        if (s_over == 2) set_error(C, POLYLLA_ERR_LIMIT, 106);
+        long_fallback(M, lab, tf, t0, i, P, F, pool, repair, C);
       }
       __syncthreads();
       continue;
     }
-    // 2. successor of every member as a member index; canonical start
+    // ---- 2. successors as member indices, tips, canonical start
     for (int a = threadIdx.x; a < L; a += blockDim.x) loc[mem[a]] = a;
-    __syncthreads();
-    unsigned long long kbest = ~0ull;
-    int ibest = -1;
     if (threadIdx.x == 0) {
-      s_ntip = 0;
-      s_tipcur = 0;
+      s_nt = 0;
+      s_fail = 0;
     }
     __syncthreads();
+    int* tip_bar = R4;
+    unsigned long long kb = ~0ull;
+    int ib = -1;
     for (int a = threadIdx.x; a < L; a += blockDim.x) {
       const int h = mem[a];
       const int sg = succ[h];
       const int g = sg & kSuccMask;
       int b = ((unsigned)g < (unsigned)H) ? loc[g] : -1;
       if (b < 0 || b >= L || mem[b] != g) {
-        set_error(C, POLYLLA_ERR_LIMIT, 102);
+        s_fail = 1;
         b = a;
       }
-      nx0[a] = b;
-      if (sg & kTipFlag) atomicAdd(&s_ntip, 1);
+      R0[a] = b;
+      if (sg & kTipFlag) tip_bar[atomicAdd(&s_nt, 1)] = h;
       const unsigned long long key = he_key(M.tri, h);
-      if (key < kbest) {
-        kbest = key;
-        ibest = a;
+      if (key < kb) {
+        kb = key;
+        ib = a;
       }
     }
     unsigned long long kmin;
     int c;
-    block_min_key(kbest, ibest, s_key, s_idx, &kmin, &c);
-    // 3. rank from the canonical start: cut the cycle before it, then jump
-    for (int a = threadIdx.x; a < L; a += blockDim.x)
-      if (nx0[a] == c) nx0[a] = -1;
-    __syncthreads();
-    int* dist = list_rank(nx0, nx1, d0, d1, L);
-    // 4. outputs: members in cycle order, polygon record, tips
+    block_min_key(kb, ib, s_key, s_idx, &kmin, &c);
+    const int nt = s_nt;
+    if (s_fail) {
+      if (threadIdx.x == 0) set_error(C, POLYLLA_ERR_LIMIT, 107);
+      __syncthreads();
+      continue;
+    }
     if (threadIdx.x == 0) {
-      s_base = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->lm_alloc),
-                                    (unsigned long long)L);
-      const int ntip = s_ntip;
+      P.mode[i] = 1;
       P.start[i] = mem[c];
       P.len[i] = L;
-      P.ntip[i] = ntip;
-      if (ntip > 0) {
-        const long long tb = (long long)atomicAdd(
-            reinterpret_cast<unsigned long long*>(&C->n_tips), (unsigned long long)ntip);
-        P.tipbase[i] = (int)tb;
+      P.ntip[i] = nt;
+      P.pcnt[i] = 0;
+      P.flen[i] = 0;
+      atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_vtx_trav), (unsigned long long)L);
+      if (nt) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_tips), (unsigned long long)nt);
         atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_tip_polys), 1ull);
       }
-      atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_vtx_trav), (unsigned long long)L);
     }
-    __syncthreads();
-    const long long base = s_base;
-    if (threadIdx.x == 0) P.lmbase[i] = (base + L <= LM.cap) ? (int)base : -1;
-    for (int a = threadIdx.x; a < L; a += blockDim.x) {
-      const int r = L - 1 - dist[a];
-      if (base + L <= LM.cap) {
-        LM.h[base + r] = mem[a];
-        LM.poly[base + r] = i;
-      }
-      const int h = mem[a];
-      if (succ[h] & kTipFlag) {
-        const int q = atomicAdd(&s_tipcur, 1);
-        const long long slot = (long long)P.tipbase[i] + q;
-        if (slot < T.cap) {
-          T.h[slot] = h;
-          T.poly[slot] = i;
-          T.vtip[M.tri[he_next(h)]] = ((long long)epoch << 32) | (unsigned)slot;
+    if (!repair || nt == 0) {
+      // ---- 3. the polygon itself, in cycle order from its canonical start
+      for (int a = threadIdx.x; a < L; a += blockDim.x)
+        if (R0[a] == c) R0[a] = -1;
+      __syncthreads();
+      const int* dist = list_rank(R0, R1, R2, R3, L);
+      if (threadIdx.x == 0)
+        s_base = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->pool_alloc),
+                                      (unsigned long long)L);
+      __syncthreads();
+      const long long base = s_base;
+      if (base + L <= pool.cap) {
+        for (int a = threadIdx.x; a < L; a += blockDim.x)
+          pool.v[base + (L - 1 - dist[a])] = M.tri[mem[a]];
+        if (threadIdx.x == 0) {
+          P.pos[i] = base;
+          P.flen[i] = L;
         }
+      } else if (threadIdx.x == 0) {
+        set_error(C, POLYLLA_ERR_LIMIT, 108);
       }
-    }
-    if (threadIdx.x == 0 && base + L > LM.cap) set_error(C, POLYLLA_ERR_LIMIT, 103);
-    __syncthreads();
-  }
-}
-
-// Members of long polygons, in cycle order, into a CSR (traversal CSR: every long
-// polygon; final CSR: long polygons without tips).
-__global__ void __launch_bounds__(kBlock) k_long_write(DevMesh M, LongMembers LM, PolyArrays P,
-                                                       const long long* __restrict__ off,
-                                                       int* __restrict__ vtx, int final_pass,
-                                                       Counters* C) {
-  const long long nm = min(C->lm_alloc, LM.cap);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = LM.poly[e];
-    if (P.mode[i] != 1) continue;
-    if (final_pass && P.ntip[i] != 0) continue;  // its pieces are written elsewhere
-    const long long r = e - P.lmbase[i];
-    const long long dst = (final_pass ? P.vb[i] : off[i]) + r;
-    vtx[dst] = M.tri[LM.h[e]];
-  }
-}
-
-// ---------------------------------------------------------------- reparation
-// Shared memory: mem[N] | A[N] | B[N] (ints) | K0[N] | K1[N] (64-bit), N <= kLongMaxMembers.
-__global__ void __launch_bounds__(kLongThreads) k_long_repair(
-    DevMesh M, const int* __restrict__ succ, PolyArrays P, TipArrays T, LongList Lg,
-    LongMembers LM, LongMembers LM2, FinalPieces F, int* __restrict__ loc, int epoch, Counters* C) {
-  extern __shared__ int smem[];
-  int* mem = smem;
-  int* A = mem + kLongMaxMembers;
-  int* B = A + kLongMaxMembers;
-  unsigned long long* K0 = reinterpret_cast<unsigned long long*>(B + kLongMaxMembers);
-  unsigned long long* K1 = K0 + kLongMaxMembers;
-  __shared__ int s_n;
-  __shared__ long long s_base;
-  const int H = (int)(3 * M.m);
-  const long long nl = min(C->n_long, Lg.cap);
-  for (long long j = blockIdx.x; j < nl; j += gridDim.x) {
-    const int i = Lg.poly[j];
-    if (P.mode[i] != 1 || P.ntip[i] == 0) continue;  // uniform across the block
-    const int L = P.len[i];
-    const long long lb = P.lmbase[i];
-    const int nt = P.ntip[i];
-    const long long tb = P.tipbase[i];
-    // 1. members: the polygon's old frontier half-edges (in cycle order), then both
-    //    half-edges of every processed split edge
-    if (threadIdx.x == 0) {
-      int w = L;
-      for (int q = 0; q < nt; ++q) {
-        const long long k = tb + q;
-        if (T.state[k] != 1 || T.o[k] < 0) continue;
-        if (w + 2 <= kLongMaxMembers) {
-          mem[w] = T.o[k];
-          mem[w + 1] = M.twin[T.o[k]];
-        }
-        w += 2;
-      }
-      s_n = w;
-    }
-    __syncthreads();
-    const int N = s_n;
-    if (N > kLongMaxMembers || lb < 0) {
-      if (threadIdx.x == 0) P.mode[i] = 2;  // the generic kernels take this polygon
       __syncthreads();
       continue;
     }
-    for (int a = threadIdx.x; a < L; a += blockDim.x) mem[a] = LM.h[lb + a];
+    // ---- 4a. split edge of every tip (labels still as traversed)
+    int* tip_b = R5;
+    int* tip_o = R6;
+    int* tip_x = R7;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      const int g = tip_bar[t];
+      const int oj = split_edge(tf, g, H);
+      tip_b[t] = M.tri[tf_twin(tf[g])];  // origin of b->a
+      tip_o[t] = oj;
+      tip_x[t] = (oj >= 0) ? M.tri[he_next(oj)] : -1;
+      if (oj < 0) s_fail = 1;
+    }
     __syncthreads();
-    for (int a = threadIdx.x; a < N; a += blockDim.x) loc[mem[a]] = a;
+    // ---- 4b. which tips are split: in increasing tip order, a tip is removed when
+    //          a split tip with a smaller id ends its split edge on it
+    int* sb = R8;          // tip vertices, sorted
+    int* st = R8 + 2048;   // their tip indices (nt <= kLM / 2)
+    if (threadIdx.x == 0) {
+      int ns = 0;
+      if (!s_fail && 2 * nt <= kLM) {
+        for (int t = 0; t < nt; ++t) {
+          sb[t] = tip_b[t];
+          st[t] = t;
+        }
+        heap_sort(sb, st, nt);
+        int* cancelled = R1;
+        for (int t = 0; t < nt; ++t) cancelled[t] = 0;
+        for (int q = 0; q < nt; ++q) {
+          const int t = st[q];
+          if (cancelled[t]) continue;
+          RQ[ns++] = t;  // chord list, increasing tip vertex
+          const int x = tip_x[t];
+          if (x > sb[q]) {  // a larger tip at x is removed by this split edge
+            int lo = q + 1, hi = nt - 1;
+            while (lo <= hi) {
+              const int mid = (lo + hi) >> 1;
+              if (sb[mid] < x) {
+                lo = mid + 1;
+              } else if (sb[mid] > x) {
+                hi = mid - 1;
+              } else {
+                cancelled[st[mid]] = 1;
+                break;
+              }
+            }
+          }
+        }
+      } else {
+        s_fail = 1;
+      }
+      s_ns = ns;
+    }
     __syncthreads();
-    // 2. successors after the splits (A) and keys (K0)
+    const int ns = s_ns;
+    const int N = L + 2 * ns;
+    if (s_fail || N > kLM) {
+      // sequential path (no split edge has been marked yet)
+      if (threadIdx.x == 0) long_fallback(M, lab, tf, t0, i, P, F, pool, repair, C);
+      __syncthreads();
+      continue;
+    }
+    // ---- 4c. mark the split edges; their endpoints' successors change
+    const int vst = -1 - epoch;  // "endpoint of a split edge" stamp of this run
+    for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+      const int t = RQ[q];
+      const int oj = tip_o[t];
+      const int tw = tf_twin(tf[oj]);
+      set_frontier(lab, tf, oj);
+      set_frontier(lab, tf, tw);
+      vstamp[tip_b[t]] = vst;
+      vstamp[tip_x[t]] = vst;
+      mem[L + 2 * q] = oj;
+      mem[L + 2 * q + 1] = tw;
+    }
+    __syncthreads();
+    for (int a = L + threadIdx.x; a < N; a += blockDim.x) loc[mem[a]] = a;
+    __syncthreads();
+    // ---- 4d. new successors (kept in R6) and each member's cycle minimum key
+    int* na = R0;
+    int* nb = R1;
+    unsigned long long* ka = reinterpret_cast<unsigned long long*>(R2);  // R2..R3
+    unsigned long long* kb2 = reinterpret_cast<unsigned long long*>(R4); // R4..R5
     for (int a = threadIdx.x; a < N; a += blockDim.x) {
-      const int g = succ[mem[a]] & kSuccMask;
+      const int h = mem[a];
+      int g;
+      if (vstamp[M.tri[he_next(h)]] == vst) {
+        long long steps = 0;
+        g = turn_tf(tf, h, H, steps, limit);
+      } else {
+        g = succ[h] & kSuccMask;
+      }
       int b = ((unsigned)g < (unsigned)H) ? loc[g] : -1;
       if (b < 0 || b >= N || mem[b] != g) {
-        set_error(C, POLYLLA_ERR_LIMIT, 110);
+        s_fail = 1;
         b = a;
       }
-      A[a] = b;
-      K0[a] = he_key(M.tri, mem[a]);
+      na[a] = b;
+      R6[a] = b;
+      ka[a] = he_key(M.tri, h);
     }
     __syncthreads();
-    // 3. every member learns its cycle's smallest key by pointer jumping
-    int rounds = 1;
-    while ((1 << rounds) < N) ++rounds;
-    {
-      int *na = A, *nb = B;
-      unsigned long long *ka = K0, *kb = K1;
-      for (int r = 0; r <= rounds; ++r) {
-        for (int a = threadIdx.x; a < N; a += blockDim.x) {
-          const int n1 = na[a];
-          const unsigned long long x = ka[n1];
-          kb[a] = (x < ka[a]) ? x : ka[a];
-          nb[a] = na[n1];
-        }
-        __syncthreads();
-        int* t = na; na = nb; nb = t;
-        unsigned long long* u = ka; ka = kb; kb = u;
-      }
-      if (ka != K0)
-        for (int a = threadIdx.x; a < N; a += blockDim.x) K0[a] = ka[a];
+    if (s_fail) {
+      if (threadIdx.x == 0) set_error(C, POLYLLA_ERR_LIMIT, 109);
       __syncthreads();
-    }
-    // A[a] = member index of a's piece's canonical start
-    for (int a = threadIdx.x; a < N; a += blockDim.x) A[a] = loc[(int)(K0[a] & 0xffffffffu)];
-    // 4. B[start] = smallest split record on the piece (names the piece)
-    for (int a = threadIdx.x; a < N; a += blockDim.x) B[a] = 0x7fffffff;
-    __syncthreads();
-    for (int a = L + threadIdx.x; a < N; a += blockDim.x) {
-      const long long tag = T.chord[mem[a]];
-      if ((int)(tag >> 32) == epoch) atomicMin(B + A[a], (int)(tag & 0xffffffffll));
-    }
-    __syncthreads();
-    // 5. ranks from each piece's canonical start (its cycle cut just before it)
-    int* nx0 = reinterpret_cast<int*>(K1);
-    int* nx1 = nx0 + kLongMaxMembers;
-    int* d0 = reinterpret_cast<int*>(K0);
-    int* d1 = d0 + kLongMaxMembers;
-    for (int a = threadIdx.x; a < N; a += blockDim.x) {
-      const int b = loc[succ[mem[a]] & kSuccMask];
-      nx0[a] = (b == A[a]) ? -1 : b;
-    }
-    __syncthreads();
-    const int* dist = list_rank(nx0, nx1, d0, d1, N);
-    // 6. piece records of every split candidate; the naming ones get start / length
-    for (int a = L + threadIdx.x; a < N; a += blockDim.x) {
-      const long long tag = T.chord[mem[a]];
-      if ((int)(tag >> 32) != epoch) continue;
-      const int q = (int)(tag & 0xffffffffll);
-      const int st = A[a];
-      const int rec = B[st];
-      T.piece[q] = rec;
-      if (rec == q) {
-        T.rec_start[q] = mem[st];
-        T.rec_len[q] = dist[st] + 1;
-      }
-    }
-    // 7. the pieces' members for the final write: (half-edge, rank, naming record)
-    if (threadIdx.x == 0)
-      s_base = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->lm2_alloc),
-                                    (unsigned long long)N);
-    __syncthreads();
-    const long long base = s_base;
-    if (base + N <= LM2.cap) {
-      for (int a = threadIdx.x; a < N; a += blockDim.x) {
-        const int st = A[a];
-        LM2.h[base + a] = mem[a];
-        LM2.poly[base + a] = B[st];
-        LM2.rank[base + a] = dist[st] - dist[a];
-      }
-    } else if (threadIdx.x == 0) {
-      set_error(C, POLYLLA_ERR_LIMIT, 111);
-    }
-    __syncthreads();
-    // 8. order the pieces (shared memory is free again): one thread, as k_poly_order
-    if (threadIdx.x == 0) {
-      const bool fits = 24ll * nt + 8 <= 7ll * kLongMaxMembers;  // ints of shared memory
-      order_pieces(M, P, T, F, C, i, fits ? smem : T.scratch + 24ll * tb, 1);
-      P.mode[i] = 3;
-    }
-    __syncthreads();
-  }
-}
-
-// Members of the pieces of long polygons into the final CSR.
-__global__ void __launch_bounds__(kBlock) k_long_write_pieces(DevMesh M, LongMembers LM2,
-                                                              TipArrays T, FinalPieces F,
-                                                              int* __restrict__ vtx, Counters* C) {
-  const long long nm = min(C->lm2_alloc, LM2.cap);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nm;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int slot = T.rec_slot[LM2.poly[e]];
-    if (slot < 0 || slot >= F.cap) {
-      set_error(C, POLYLLA_ERR_LIMIT, 112);
       continue;
     }
-    vtx[F.off[slot] + LM2.rank[e]] = M.tri[LM2.h[e]];
+    {
+      int rounds = 1;
+      while ((1 << rounds) < N) ++rounds;
+      int *pa = na, *pb = nb;
+      unsigned long long *qa = ka, *qb = kb2;
+      for (int r = 0; r <= rounds; ++r) {
+        for (int a = threadIdx.x; a < N; a += blockDim.x) {
+          const int n1 = pa[a];
+          const unsigned long long x = qa[n1];
+          qb[a] = (x < qa[a]) ? x : qa[a];
+          pb[a] = pa[n1];
+        }
+        __syncthreads();
+        int* t = pa; pa = pb; pb = t;
+        unsigned long long* u = qa; qa = qb; qb = u;
+      }
+      for (int a = threadIdx.x; a < N; a += blockDim.x)
+        R7[a] = loc[(int)(qa[a] & 0xffffffffu)];
+    }
+    __syncthreads();
+    int* A = R7;  // canonical start (member index) of each member's piece
+    int* B = R8;  // piece name, at its start: the smallest split member on the piece
+    for (int a = threadIdx.x; a < N; a += blockDim.x) B[a] = 0x7fffffff;
+    __syncthreads();
+    for (int a = L + threadIdx.x; a < N; a += blockDim.x) atomicMin(B + A[a], a);
+    // ---- 4e. ranks in the pieces (each cycle cut just before its start)
+    for (int a = threadIdx.x; a < N; a += blockDim.x) R0[a] = (R6[a] == A[a]) ? -1 : R6[a];
+    __syncthreads();
+    const int* dist = list_rank(R0, R1, R2, R3, N);
+    int* pos = (dist == R2) ? R3 : R2;  // the free one of the ranking buffers
+    int* nodeof = R0;                        // piece name - L -> node
+    // ---- 4f. order of the pieces, pool and piece records (one thread)
+    if (threadIdx.x == 0) {
+      const int W = 2 * ns + 1;
+      int* node_name = R1;
+      int* uf = R4;
+      int* left = R5;
+      int* right = R6;
+      int* cnt = RQ;
+      int npieces = 0;
+      bool bad = false;
+      for (int q = 0; q < 2 * ns; ++q) nodeof[q] = -1;
+      for (int q = 0; q < 2 * ns && !bad; ++q) {
+        const int name = B[A[L + q]];
+        if (name < L || name >= N) {
+          bad = true;
+          break;
+        }
+        if (nodeof[name - L] < 0) {
+          nodeof[name - L] = npieces;
+          node_name[npieces++] = name;
+        }
+      }
+      if (bad || npieces != ns + 1) {
+        set_error(C, POLYLLA_ERR_LIMIT, 110);
+        s_fail = 1;
+      } else {
+        for (int v = 0; v < npieces; ++v) {
+          uf[v] = v;
+          pos[v] = v;
+        }
+        int nodes = npieces;
+        for (int q = ns - 1; q >= 0 && !bad; --q) {  // decreasing tip vertex
+          int ra = nodeof[B[A[L + 2 * q]] - L];
+          int rb = nodeof[B[A[L + 2 * q + 1]] - L];
+          while (uf[ra] != ra) ra = uf[ra] = uf[uf[ra]];
+          while (uf[rb] != rb) rb = uf[rb] = uf[uf[rb]];
+          if (ra == rb || nodes >= W) {
+            bad = true;
+            break;
+          }
+          const int u = nodes++;
+          left[u] = pos[ra];
+          right[u] = pos[rb];
+          uf[rb] = ra;
+          pos[ra] = u;
+        }
+        if (bad) {
+          set_error(C, POLYLLA_ERR_LIMIT, 111);
+          s_fail = 1;
+        } else {
+          for (int v = 0; v < npieces; ++v) cnt[v] = 1;
+          for (int u = npieces; u < nodes; ++u) cnt[u] = cnt[left[u]] + cnt[right[u]];
+          pos[nodes - 1] = 0;
+          for (int u = nodes - 1; u >= npieces; --u) {
+            pos[left[u]] = pos[u];
+            pos[right[u]] = pos[u] + cnt[left[u]];
+          }
+          const long long base = (long long)atomicAdd(
+              reinterpret_cast<unsigned long long*>(&C->pool_alloc), (unsigned long long)N);
+          const long long fb = (long long)atomicAdd(
+              reinterpret_cast<unsigned long long*>(&C->fslot_alloc), (unsigned long long)npieces);
+          if (base + N > pool.cap || fb + npieces > F.cap) {
+            set_error(C, POLYLLA_ERR_LIMIT, 112);
+            s_fail = 1;
+          } else {
+            for (int v = 0; v < npieces; ++v) cnt[pos[v]] = dist[A[node_name[v]]] + 1;
+            long long acc = base;
+            for (int p = 0; p < npieces; ++p) {
+              F.pos[fb + p] = acc;
+              F.len[fb + p] = cnt[p];
+              acc += cnt[p];
+            }
+            s_fbase = fb;
+            P.pcnt[i] = npieces;
+            P.pbase[i] = (int)fb;
+            P.flen[i] = N;
+            atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)ns);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_fail) {
+      __syncthreads();
+      continue;
+    }
+    // ---- 4g. members to the pool: piece position + rank from the piece's start
+    const long long fb = s_fbase;
+    for (int a = threadIdx.x; a < N; a += blockDim.x) {
+      const int s0 = A[a];
+      const int node = nodeof[B[s0] - L];
+      pool.v[F.pos[fb + pos[node]] + (dist[s0] - dist[a])] = M.tri[mem[a]];
+    }
+    __syncthreads();
   }
 }
 
-cudaError_t launch_long_write_pieces(const DevMesh& M, const LongMembers& LM2, const TipArrays& T,
-                                     const FinalPieces& F, int* vtx, Counters* C, int grid,
-                                     cudaStream_t s) {
-  k_long_write_pieces<<<grid, kBlock, 0, s>>>(M, LM2, T, F, vtx, C);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_long_trav(const DevMesh& M, const int* tf, const int* seeds, const int* succ,
-                             const PolyArrays& P, const TipArrays& T, const LongList& Lg,
-                             const LongMembers& LM, int* visit, int* loc, int epoch, Counters* C,
-                             int grid, cudaStream_t s) {
-  const size_t smem = sizeof(int) * (size_t)(kLongMaxTri + 5 * kLongMaxMembers);
+cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
+                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                        const LongList& Lg, int* visit, int* loc, int* vstamp, int epoch,
+                        int repair, Counters* C, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(int) * (size_t)kLongSmemInts;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_long_trav, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_long_trav<<<grid, kLongThreads, smem, s>>>(M, tf, seeds, succ, P, T, Lg, LM, visit, loc, epoch,
-                                               C);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_long_write(const DevMesh& M, const LongMembers& LM, const PolyArrays& P,
-                              const long long* off, int* vtx, int final_pass, Counters* C, int grid,
-                              cudaStream_t s) {
-  k_long_write<<<grid, kBlock, 0, s>>>(M, LM, P, off, vtx, final_pass, C);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_long_repair(const DevMesh& M, const int* succ, const PolyArrays& P,
-                               const TipArrays& T, const LongList& Lg, const LongMembers& LM,
-                               const LongMembers& LM2, const FinalPieces& F, int* loc, int epoch,
-                               Counters* C, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(int) * (size_t)(3 * kLongMaxMembers) +
-                      sizeof(unsigned long long) * (size_t)(2 * kLongMaxMembers);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_long_repair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
-  k_long_repair<<<grid, kLongThreads, smem, s>>>(M, succ, P, T, Lg, LM, LM2, F, loc, epoch, C);
+  k_long<<<grid, kLongThreads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, visit, loc,
+                                          vstamp, epoch, repair, C);
   return cudaGetLastError();
 }
 

@@ -28,13 +28,13 @@ struct Counters {
   long long n_tip_polys;  // polygons with >= 1 barrier-edge tip
   long long n_tips;
   long long n_splits;
-  long long n_poly;       // final polygons
-  long long n_vtx;        // final total length
-  long long piece_alloc;  // final piece slots handed out
-  long long n_pairs;      // (tip -> tip) split-edge pairs found by reparation
+  long long n_poly;       // output polygons
+  long long n_vtx;        // output total length
+  long long pool_alloc;   // vertex pool entries handed out
+  long long fslot_alloc;  // piece records handed out
   long long n_long;       // polygons longer than the walk cap
-  long long lm_alloc;     // members of long polygons written
-  long long lm2_alloc;    // members of long polygons' pieces written
+  long long n_defer;      // polygons with one tip, left to k_repair_one
+  long long n_multi;      // polygons with several tips, left to k_repair_multi
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
   int error;              // first device error (polylla_status), 0 if none
@@ -123,19 +123,33 @@ cudaError_t launch_scan_tiles(const long long* tile_sum, long long* tile_off, lo
                               const long long* n_dev, int tile, long long* tot0, long long* tot1,
                               long long* end, int end_mode, long long end_cap, Counters* C,
                               cudaStream_t s);
-// Per traversal polygon (index = seed order), capacity m.
+// Per polygon of the traversal (index = seed order), capacity m.
 struct PolyArrays {
-  int* start;     // canonical start half-edge
+  int* start;     // canonical start half-edge of the traversal polygon
   int* len;       // traversal length
-  int* ntip;      // barrier-edge tips on the cycle
-  int* tipbase;   // first entry of its tips in the tip list
-  int* pbase;     // first final piece slot (polygons with tips)
-  int* pcnt;      // final pieces
-  int* flen;      // total length of the final pieces
-  long long* vb;  // output vertex offset
-  int* mode;      // 0 walked by one thread; 1 long (one block); 2 long, generic
-                  // kernels; 3 long with pieces from the block's reparation
-  int* lmbase;    // first entry of a long polygon's members (cycle order)
+  int* ntip;      // barrier-edge tips
+  int* tip_h;     // barrier half-edge ending at the smallest tip vertex, or -1
+  int* mode;      // 0 one thread; 1 one block (long.cu); 2 long, one thread of a block
+  int* pcnt;      // output pieces: 0 = the polygon itself, at pos; else records at pbase
+  int* pbase;     // first piece record
+  int* flen;      // total output length
+  long long* pos; // pool position of an unsplit polygon
+};
+
+// Output pieces of split polygons: pool position and length (capacity n + m).
+struct FinalPieces {
+  long long* pos;
+  int* len;
+  int* h;  // start half-edges while a polygon is being split
+  long long cap;
+};
+
+// Vertex pool: every output polygon is written here first, in its final order,
+// by the thread (or block) that walked it; the CSR is a copy.  Capacity 6m + 2n:
+// the output (at most 3m + 2n) plus staging for one-tip polygons (at most 3m).
+struct Pool {
+  int* v;
+  long long cap;
 };
 
 // Polygons longer than the walk cap (capacity m).
@@ -144,90 +158,30 @@ struct LongList {
   long long cap;
 };
 
-// Members of long polygons (or of their pieces): half-edge, owner, rank.
-struct LongMembers {
-  int* h;
-  int* poly;  // polygon (traversal) or naming record (pieces)
-  int* rank;  // rank in the piece (pieces only)
-  long long cap;
-};
-
-// Barrier-edge tips (capacity = n vertices), grouped by polygon.
-struct TipArrays {
-  int* h;              // barrier half-edge a->b ending at the tip b
-  int* poly;           // polygon of the tip
-  int* o;              // split half-edge b->x, or -1
-  int* state;          // 1 processed, 0 cancelled
-  int* piece;          // [2 per tip] record naming the piece on each side
-  int* rec_start;      // [2 per tip] canonical start of the named piece
-  int* rec_len;        // [2 per tip] its length
-  int* rec_slot;       // [2 per tip] final piece slot of a naming record
-  int* pair_src;       // (tip -> tip) pairs
-  int* pair_dst;
-  int* cancel_round;
-  int* scratch;        // [24 per tip] per-polygon ordering scratch
-  long long* vtip;     // [n] (epoch << 32 | tip entry) of the vertex's tip
-  long long* chord;    // [3m] (epoch << 32 | record) of split half-edges
-  long long cap;
-};
-
-// Final pieces of split polygons (capacity m + 1).
-struct FinalPieces {
-  int* start;
-  int* len;
-  long long* off;
-  int* src;  // 0 written by a walk, 1 from a long polygon's member list
-  long long cap;
-};
-
 cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
                         cudaStream_t s);
-cudaError_t launch_trav_count(const DevMesh& M, const uint8_t* lab, const int* seeds,
-                              const int* succ, const PolyArrays& P, const TipArrays& T,
-                              const LongList& Lg, int epoch, Counters* C, int grid,
-                              cudaStream_t s);
-cudaError_t launch_long_trav(const DevMesh& M, const int* tf, const int* seeds, const int* succ,
-                             const PolyArrays& P, const TipArrays& T, const LongList& Lg,
-                             const LongMembers& LM, int* visit, int* loc, int epoch, Counters* C,
-                             int grid, cudaStream_t s);
-cudaError_t launch_long_write(const DevMesh& M, const LongMembers& LM, const PolyArrays& P,
-                              const long long* off, int* vtx, int final_pass, Counters* C, int grid,
-                              cudaStream_t s);
-cudaError_t launch_long_repair(const DevMesh& M, const int* succ, const PolyArrays& P,
-                               const TipArrays& T, const LongList& Lg, const LongMembers& LM,
-                               const LongMembers& LM2, const FinalPieces& F, int* loc, int epoch,
-                               Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_long_write_pieces(const DevMesh& M, const LongMembers& LM2, const TipArrays& T,
-                                     const FinalPieces& F, int* vtx, Counters* C, int grid,
-                                     cudaStream_t s);
-cudaError_t launch_len_tiles(const int* len, long long* tile_sum, Counters* C, int grid,
-                             cudaStream_t s);
-cudaError_t launch_offsets(const int* len, const long long* tile_off, long long* off, Counters* C,
-                           int grid, cudaStream_t s);
-cudaError_t launch_trav_write(const DevMesh& M, const int* succ, const int* start, const int* len,
-                              const int* mode, const long long* off, int* vtx, Counters* C,
-                              int grid, cudaStream_t s);
-cudaError_t launch_tip_split(const DevMesh& M, const uint8_t* lab, const TipArrays& T, int epoch,
-                             Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_tip_resolve(const TipArrays& T, Counters* C, cudaStream_t s);
-cudaError_t launch_tip_mark(const DevMesh& M, uint8_t* lab, const TipArrays& T, int epoch,
-                            Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_resucc(const DevMesh& M, const uint8_t* lab, int* succ, const TipArrays& T,
-                          Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_piece_walk(const DevMesh& M, const int* succ, const PolyArrays& P,
-                              const TipArrays& T, int epoch, Counters* C, int grid,
-                              cudaStream_t s);
-cudaError_t launch_poly_order(const DevMesh& M, const PolyArrays& P, const TipArrays& T,
-                              const FinalPieces& F, Counters* C, int grid, cudaStream_t s);
+// One thread per seed: walk (<= kWalkCap) and, if `repair`, split the polygon.
+cudaError_t launch_walk(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
+                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                        const LongList& Lg, const LongList& D1, const LongList& Dm, int repair,
+                        Counters* C, int grid, cudaStream_t s);
+// One thread per polygon with one tip / with several tips (listed by k_walk).
+cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
+                              const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                              const LongList& D1, Counters* C, int sms, cudaStream_t s);
+cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
+                                const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                                const LongList& Dm, Counters* C, int sms, cudaStream_t s);
+// One block per long polygon: gather, rank and, if `repair`, split.
+cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
+                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                        const LongList& Lg, int* visit, int* loc, int* vstamp, int epoch,
+                        int repair, Counters* C, int grid, cudaStream_t s);
+// Output: per-tile (polygon count, vertex count); then offsets and the copy.
 cudaError_t launch_final_tiles(const PolyArrays& P, long long* tile_sum, Counters* C, int grid,
                                cudaStream_t s);
-cudaError_t launch_final_offsets(const PolyArrays& P, const FinalPieces& F,
-                                 const long long* tile_off, long long* off, long long m,
-                                 Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_final_write_polys(const DevMesh& M, const int* succ, const PolyArrays& P,
-                                     const long long* off_trav, const int* vtx_trav, int* vtx,
-                                     Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_final_write_pieces(const DevMesh& M, const int* succ, const FinalPieces& F,
-                                      int* vtx, Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                               const long long* tile_off, long long* off, int* vtx, long long m,
+                               Counters* C, int grid, cudaStream_t s);
 
 }  // namespace polylla

@@ -1,0 +1,579 @@
+// Traversal (Section 3.2.2, Algorithms 3 and 4) and, for ordinary polygons,
+// reparation (Section 3.2.3, Algorithm 5) in one pass.
+//
+//   k_succ  one thread per triangle: for each frontier half-edge, the next
+//           frontier half-edge of its region's boundary (PolyConstruction's
+//           turn), with the barrier-edge tip flag.  The three turns of a triangle
+//           advance together so their loads overlap.
+//   k_walk  one thread per seed: enter the region, chase succ around the cycle
+//           (at most kWalkCap vertices, staged in shared memory), note the
+//           canonical start and the tips.  A polygon without tips (or any, when no
+//           reparation is asked for) is copied, rotated to its canonical start,
+//           into the vertex pool, whose space is handed out per warp.  A polygon
+//           with tips is listed -- one tip (about 90% of them) or several -- so
+//           that the dependent loads of a split do not stall the 31 other lanes of
+//           its warp; a longer one is left to one thread block (long.cu).
+//   k_repair_one    one thread per polygon with one tip: split it and chase the
+//           two arcs of the cycle at once.
+//   k_repair_multi  one thread per polygon with several tips: the cycle becomes
+//           a linked list of nodes in shared memory, and each split (smallest tip
+//           of the current piece first) adds two chord nodes and relinks four
+//           pointers.
+// The paper's AtomicAdd on i_Gmesh / i_Gpos is replaced by the output scan
+// (final.cu); the pool order does not matter.
+#include "walk.cuh"
+
+namespace polylla {
+
+__global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const int* __restrict__ tf,
+                                                 int* __restrict__ succ, Counters* C) {
+  const long long m = M.m;
+  const int H = (int)(3 * m);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    int x[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k] = __ldg(tf + 3 * t + k);
+    int cur[3], y[3];
+    unsigned active = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cur[k] = 0;
+      y[k] = 0;
+      if (x[k] >= 0) continue;  // not frontier: no successor
+      const int kn = (k == 2) ? 0 : k + 1;
+      cur[k] = (int)(3 * t + kn);
+      y[k] = x[kn];
+      active |= 1u << k;
+    }
+    for (long long step = 0; active && step <= 3 * m; ++step) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (!((active >> k) & 1u)) continue;
+        if (y[k] < 0) {  // reached a frontier half-edge
+          const int g = cur[k];
+          succ[3 * t + k] = (g == tf_twin(x[k])) ? (g | kTipFlag) : g;
+          active &= ~(1u << k);
+          continue;
+        }
+        if (y[k] >= H) {
+          set_error(C, POLYLLA_ERR_LIMIT, 50);
+          succ[3 * t + k] = (int)(3 * t + k);
+          active &= ~(1u << k);
+          continue;
+        }
+        cur[k] = he_next(y[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if ((active >> k) & 1u) y[k] = tf[cur[k]];
+    }
+    if (active) set_error(C, POLYLLA_ERR_LIMIT, 50);
+  }
+}
+
+cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
+                        cudaStream_t s) {
+  k_succ<<<grid, kBlock, 0, s>>>(M, tf, succ, C);
+  return cudaGetLastError();
+}
+
+// Warp-aggregated allocation: each lane asks for `need` entries; one atomic per
+// warp.  All 32 lanes must call it.
+__device__ __forceinline__ long long warp_alloc(long long* counter, int need) {
+  const int lane = threadIdx.x & 31;
+  int incl = need;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total > 0)
+    base = atomicAdd(reinterpret_cast<unsigned long long*>(counter), (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return (long long)base + incl - need;
+}
+
+constexpr int kWalkThreads = 256;
+
+__global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, uint8_t* lab, int* tf,
+                                                       const int* __restrict__ seeds,
+                                                       const int* __restrict__ succ, PolyArrays P,
+                                                       FinalPieces F, Pool pool, LongList Lg,
+                                                       LongList D1, LongList Dm, int repair,
+                                                       Counters* C) {
+  extern __shared__ int sbuf[];
+  int* my = sbuf + threadIdx.x * kWalkCap;
+  const long long n = C->n_seeds;
+  const int H = (int)(3 * M.m);
+  const long long limit = 3 * M.m + 3;
+  unsigned st_len = 0, st_tips = 0, st_tippolys = 0;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    int len = 0, ntips = 0, tip_h = -1, rank0 = 0, start = 0;
+    bool closed = false, is_long = false;
+    if (i < n) {
+      const int e = region_entry_tf(tf, seeds[i], H, limit);
+      if (e < 0) {
+        set_error(C, POLYLLA_ERR_LIMIT, 51);
+      } else {
+        unsigned long long best = ~0ull;
+        int tipv = 0x7fffffff;
+        int h = e;
+        bool ok = true;
+        do {
+          const int o = M.tri[h];
+          my[len] = o;
+          const unsigned long long key = ((unsigned long long)(unsigned)o << 32) | (unsigned)h;
+          if (key < best) {
+            best = key;
+            rank0 = len;
+          }
+          const int sg = succ[h];
+          const int g = sg & kSuccMask;
+          if (sg & kTipFlag) {
+            ++ntips;
+            const int b = M.tri[g];  // dest(h) = origin(twin(h))
+            if (b < tipv) {
+              tipv = b;
+              tip_h = h;
+            }
+          }
+          ++len;
+          if ((unsigned)g >= (unsigned)H) {
+            ok = false;
+            break;
+          }
+          h = g;
+        } while (h != e && len < kWalkCap);
+        closed = ok && h == e;
+        is_long = ok && !closed;
+        if (!ok) set_error(C, POLYLLA_ERR_LIMIT, 52);
+        start = (int)(best & 0xffffffffu);
+      }
+    }
+    const bool split = closed && repair && ntips > 0;
+    const int need = (closed && !split) ? len : 0;
+    const long long off = warp_alloc(&C->pool_alloc, need);
+    if (i >= n) continue;
+    if (is_long) {
+      P.mode[i] = 1;
+      P.len[i] = 0;
+      P.ntip[i] = 0;
+      P.pcnt[i] = 0;
+      P.flen[i] = 0;
+      const long long j = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_long), 1ull);
+      if (j < Lg.cap) Lg.poly[j] = (int)i;
+      continue;
+    }
+    P.mode[i] = 0;
+    P.start[i] = start;
+    P.len[i] = closed ? len : 0;
+    P.ntip[i] = closed ? ntips : 0;
+    P.tip_h[i] = tip_h;
+    P.pcnt[i] = 0;
+    P.flen[i] = 0;
+    if (!closed) continue;
+    st_len += len;
+    st_tips += ntips;
+    st_tippolys += ntips > 0;
+    if (split) {
+      LongList& D = (ntips == 1) ? D1 : Dm;
+      long long* cnt = (ntips == 1) ? &C->n_defer : &C->n_multi;
+      const long long d = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cnt), 1ull);
+      if (d < D.cap) D.poly[d] = (int)i;
+      else set_error(C, POLYLLA_ERR_LIMIT, 55);
+      continue;
+    }
+    if (off + need > pool.cap) {
+      set_error(C, POLYLLA_ERR_LIMIT, 53);
+      continue;
+    }
+    {
+      int* out = pool.v + off;
+      int r = rank0;
+      for (int q = 0; q < len; ++q) {
+        out[q] = my[r];
+        if (++r == len) r = 0;
+      }
+      P.pos[i] = off;
+      P.flen[i] = len;
+    }
+  }
+  st_len = __reduce_add_sync(0xffffffffu, st_len);
+  st_tips = __reduce_add_sync(0xffffffffu, st_tips);
+  st_tippolys = __reduce_add_sync(0xffffffffu, st_tippolys);
+  if ((threadIdx.x & 31) == 0) {
+    if (st_len) atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_vtx_trav), (unsigned long long)st_len);
+    if (st_tips) atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_tips), (unsigned long long)st_tips);
+    if (st_tippolys)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_tip_polys), (unsigned long long)st_tippolys);
+  }
+}
+
+cudaError_t launch_walk(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
+                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                        const LongList& Lg, const LongList& D1, const LongList& Dm, int repair,
+                        Counters* C, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(int) * (size_t)kWalkThreads * kWalkCap;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_walk<<<grid, kWalkThreads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, D1, Dm, repair,
+                                          C);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ unsigned long long vkey(int origin, int h) {
+  return ((unsigned long long)(unsigned)origin << 32) | (unsigned)h;
+}
+
+// One tip p = a->b, split along oj = b->x (tw = x->b), with q = turn(oj) and
+// pn = twin(p) = b->a.  The two pieces are
+//     oj, q, succ(q), ..., p          and          tw, pn, succ(pn), ..., pred(q)
+// (the boundary walk with oj, tw frontier); the other frontier half-edges keep
+// their turns, so both arcs follow the precomputed succ.  The arcs are chased
+// together; their origins are staged in the polygon's pool space (arc 1 from
+// the front, arc 2 from the back) and each piece is then copied from its
+// canonical start.  Pool space: 2L + 2 (pieces, then staging).
+__global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, int* tf,
+                                                       const int* __restrict__ succ, PolyArrays P,
+                                                       FinalPieces F, Pool pool, LongList D1,
+                                                       Counters* C) {
+  const long long nd = min(C->n_defer, D1.cap);
+  const int H = (int)(3 * M.m);
+  const long long limit = 3 * M.m + 3;
+  unsigned st_bad = 0;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nd;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long d = base + threadIdx.x;
+    const long long i = (d < nd) ? D1.poly[d] : -1;
+    const int L = (i >= 0) ? P.len[i] : 0;
+    const long long off = warp_alloc(&C->pool_alloc, i >= 0 ? 2 * L + 2 : 0);
+    const long long foff = warp_alloc(&C->fslot_alloc, i >= 0 ? 2 : 0);
+    if (i < 0) continue;
+    if (off + 2 * L + 2 > pool.cap || foff + 2 > F.cap || L < 3) {
+      set_error(C, POLYLLA_ERR_LIMIT, 56);
+      continue;
+    }
+    const int tp = P.tip_h[i];
+    if ((unsigned)tp >= (unsigned)H) {
+      set_error(C, POLYLLA_ERR_LIMIT, 57);
+      continue;
+    }
+    const int pn = tf_twin(tf[tp]);
+    const int b = M.tri[he_next(tp)];
+    const int oj = split_edge(tf, tp, H);
+    if (oj < 0 || pn >= H) {
+      set_error(C, POLYLLA_ERR_LIMIT, 54);
+      continue;
+    }
+    const int tw = tf_twin(tf[oj]);
+    const int x = M.tri[he_next(oj)];
+    if (tw >= H) {
+      set_error(C, POLYLLA_ERR_LIMIT, 54);
+      continue;
+    }
+    set_frontier(lab, tf, oj);
+    set_frontier(lab, tf, tw);
+    long long steps = 0;
+    const int g = turn_tf(tf, oj, H, steps, limit);
+    if (g < 0 || g == tw || g == pn) {
+      set_error(C, POLYLLA_ERR_LIMIT, 54);
+      continue;
+    }
+    int* stage = pool.v + off + L + 2;
+    int c1 = g, c2 = pn, n1 = 0, n2 = 0;
+    bool a1 = true, a2 = true;
+    unsigned long long b1 = vkey(b, oj), b2 = vkey(x, tw);
+    int r1 = 0, r2 = 0;
+    for (int it = 0; (a1 || a2) && it < L; ++it) {
+      const int o1 = a1 ? M.tri[c1] : 0;
+      const int s1 = a1 ? succ[c1] : 0;
+      const int o2 = a2 ? M.tri[c2] : 0;
+      const int s2 = a2 ? succ[c2] : 0;
+      if (a1) {
+        stage[n1] = o1;
+        const unsigned long long k = vkey(o1, c1);
+        ++n1;
+        if (k < b1) {
+          b1 = k;
+          r1 = n1;
+        }
+        if (c1 == tp) a1 = false;
+        else c1 = s1 & kSuccMask;
+      }
+      if (a2) {
+        ++n2;
+        stage[L - n2] = o2;
+        const unsigned long long k = vkey(o2, c2);
+        if (k < b2) {
+          b2 = k;
+          r2 = n2;
+        }
+        c2 = s2 & kSuccMask;
+        if (c2 == g) a2 = false;
+      }
+      if ((unsigned)c1 >= (unsigned)H || (unsigned)c2 >= (unsigned)H) break;
+    }
+    if (a1 || a2 || n1 + n2 != L) {
+      ++st_bad;
+      continue;
+    }
+    // piece 1 = [b, stage[0..n1)], piece 2 = [x, stage[L-1], ..., stage[L-n2]]
+    int* out = pool.v + off;
+    const int l1 = n1 + 1, l2 = n2 + 1;
+    int k = r1;
+    for (int q = 0; q < l1; ++q) {
+      out[q] = k ? stage[k - 1] : b;
+      if (++k == l1) k = 0;
+    }
+    k = r2;
+    for (int q = 0; q < l2; ++q) {
+      out[l1 + q] = k ? stage[L - k] : x;
+      if (++k == l2) k = 0;
+    }
+    F.pos[foff] = off;
+    F.len[foff] = l1;
+    F.pos[foff + 1] = off + l1;
+    F.len[foff + 1] = l2;
+    P.pcnt[i] = 2;
+    P.pbase[i] = (int)foff;
+    P.flen[i] = L + 2;
+  }
+  if (st_bad) set_error(C, POLYLLA_ERR_LIMIT, 58);
+  // one split per polygon of this list
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nd > 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)nd);
+}
+
+// Linked-list reparation of one polygon with several tips per thread.
+//
+// Nodes 0..L-1 are the polygon's frontier half-edges in boundary order from its
+// canonical start (bit 31 set on a barrier-edge tip a->b, i.e. the node followed
+// by twin(a->b)); nodes kWalkCap.. are chord half-edges added by splits.  Each
+// node keeps its half-edge, its origin vertex and next/prev links, all in shared
+// memory, transposed ([node][thread]) so that lanes at the same step hit distinct
+// banks.  The pieces form an ordered list of start nodes, as in repair_seq: the
+// first piece with a tip is split at its smallest tip b (the destination of tip
+// node p) along oj = split_edge(), and is replaced by the piece from oj (b->x)
+// followed by the piece from tw = twin(oj) (x->b).  With q the node of turn(oj)
+// -- the first frontier half-edge after oj around x -- and qp its predecessor:
+//     p -> oj -> q   and   qp -> tw -> next(p),
+// which is the boundary that walking the region with the new frontier edge gives.
+// A split removes the tip at p, and the one at qp if x was a tip, and creates
+// none (x always has a frontier edge of the region besides the chord), so only
+// those two flags change.
+constexpr int kRsThreads = 64;
+constexpr int kRsMaxSplit = 8;  // more tips: the walking repair_seq
+constexpr int kRsNodes = kWalkCap + 2 * kRsMaxSplit;
+constexpr int kRsList = kRsMaxSplit + 2;
+constexpr size_t kRsSmem =
+    (size_t)kRsThreads * (kRsNodes * (2 * sizeof(int) + 2) + kRsList);
+
+__global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t* lab, int* tf,
+                                                             const int* __restrict__ succ,
+                                                             PolyArrays P, FinalPieces F,
+                                                             Pool pool, LongList Dm,
+                                                             Counters* C) {
+  extern __shared__ int rs_smem[];
+  int* nh = rs_smem;                                   // [kRsNodes][kRsThreads]
+  int* no = nh + kRsNodes * kRsThreads;                // origins
+  uint8_t* nx = reinterpret_cast<uint8_t*>(no + kRsNodes * kRsThreads);
+  uint8_t* pv = nx + kRsNodes * kRsThreads;
+  uint8_t* ps = pv + kRsNodes * kRsThreads;            // [kRsList][kRsThreads]
+  const int t = threadIdx.x;
+#define NH(j) nh[(j) * kRsThreads + t]
+#define NO(j) no[(j) * kRsThreads + t]
+#define NX(j) nx[(j) * kRsThreads + t]
+#define PV(j) pv[(j) * kRsThreads + t]
+#define PS(j) ps[(j) * kRsThreads + t]
+  const long long nd = min(C->n_multi, Dm.cap);
+  const int H = (int)(3 * M.m);
+  const long long limit = 3 * M.m + 3;
+  unsigned st_splits = 0;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nd;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long d = base + t;
+    const long long i = (d < nd) ? Dm.poly[d] : -1;
+    const int L = (i >= 0) ? P.len[i] : 0;
+    const int nt = (i >= 0) ? P.ntip[i] : 0;
+    const long long off = warp_alloc(&C->pool_alloc, i >= 0 ? L + 2 * nt : 0);
+    const long long foff = warp_alloc(&C->fslot_alloc, i >= 0 ? nt + 1 : 0);
+    if (i < 0) continue;
+    if (off + L + 2 * nt > pool.cap || foff + nt + 1 > F.cap) {
+      set_error(C, POLYLLA_ERR_LIMIT, 56);
+      continue;
+    }
+    int cnt;
+    if (nt > kRsMaxSplit || L > kWalkCap || L < 3) {
+      const Cyc first{P.start[i], L, P.tip_h[i], nt, true};
+      cnt = repair_seq(M.tri, tf, lab, first, nt + 1, H, limit, F.h + foff, F.pos + foff,
+                       F.len + foff, pool.v + off, off);
+    } else {
+      cnt = -1;
+      bool bad = false;
+      {
+        int h = P.start[i];
+        for (int j = 0; j < L; ++j) {
+          if ((unsigned)h >= (unsigned)H) {
+            bad = true;
+            break;
+          }
+          const int sg = succ[h];
+          NH(j) = h | (sg & kTipFlag);
+          NO(j) = M.tri[h];
+          NX(j) = (uint8_t)(j + 1 == L ? 0 : j + 1);
+          PV(j) = (uint8_t)(j == 0 ? L - 1 : j - 1);
+          h = sg & kSuccMask;
+        }
+        if (h != P.start[i]) bad = true;
+      }
+      int nn = kWalkCap;  // next chord node
+      int count = 1;
+      PS(0) = 0;
+      long long acc = 0;
+      int j = 0;
+      while (!bad && j < count) {
+        const int s0 = PS(j);
+        int tb = 0x7fffffff, tipn = -1, keyn = s0, len = 0;
+        unsigned long long best = ~0ull;
+        int v = s0;
+        do {
+          const int x = NH(v);
+          const int nv = NX(v);
+          if (x < 0) {
+            const int b = NO(nv);
+            if (b < tb) {
+              tb = b;
+              tipn = v;
+            }
+          }
+          const unsigned long long key = vkey(NO(v), x & kSuccMask);
+          if (key < best) {
+            best = key;
+            keyn = v;
+          }
+          ++len;
+          v = nv;
+        } while (v != s0 && len <= kRsNodes);
+        if (len > kRsNodes) {
+          bad = true;
+          break;
+        }
+        if (tipn < 0) {  // finished piece: its origins from the canonical start
+          int* out = pool.v + off + acc;
+          v = keyn;
+          for (int k = 0; k < len; ++k) {
+            out[k] = NO(v);
+            v = NX(v);
+          }
+          F.pos[foff + j] = off + acc;
+          F.len[foff + j] = len;
+          acc += len;
+          ++j;
+          continue;
+        }
+        if (count + 1 > nt + 1 || nn + 2 > kRsNodes) {
+          bad = true;
+          break;
+        }
+        const int oj = split_edge(tf, NH(tipn) & kSuccMask, H);
+        if (oj < 0) {
+          bad = true;
+          break;
+        }
+        const int tw = tf_twin(tf[oj]);
+        if (tw >= H) {
+          bad = true;
+          break;
+        }
+        set_frontier(lab, tf, oj);
+        set_frontier(lab, tf, tw);
+        long long steps = 0;
+        const int g = turn_tf(tf, oj, H, steps, limit);
+        if (g < 0 || g == tw) {
+          bad = true;
+          break;
+        }
+        int q = -1;
+        for (int k = 0; k < L; ++k)
+          if ((NH(k) & kSuccMask) == g) q = k;
+        for (int k = kWalkCap; k < nn; ++k)
+          if (NH(k) == g) q = k;
+        if (q < 0) {
+          bad = true;
+          break;
+        }
+        const int qp = PV(q);
+        const int pn = NX(tipn);
+        const int u = nn, w = nn + 1;
+        nn += 2;
+        NH(u) = oj;
+        NO(u) = tb;
+        NH(w) = tw;
+        NO(w) = M.tri[tw];
+        NX(tipn) = (uint8_t)u;
+        PV(u) = (uint8_t)tipn;
+        NX(u) = (uint8_t)q;
+        PV(q) = (uint8_t)u;
+        NX(qp) = (uint8_t)w;
+        PV(w) = (uint8_t)qp;
+        NX(w) = (uint8_t)pn;
+        PV(pn) = (uint8_t)w;
+        NH(tipn) &= kSuccMask;
+        NH(qp) &= kSuccMask;
+        for (int k = count; k > j + 1; --k) PS(k) = PS(k - 1);
+        PS(j) = (uint8_t)u;
+        PS(j + 1) = (uint8_t)w;
+        ++count;
+      }
+      if (!bad) cnt = count;
+    }
+#undef NH
+#undef NO
+#undef NX
+#undef PV
+#undef PS
+    if (cnt < 0) {
+      set_error(C, POLYLLA_ERR_LIMIT, 54);
+      continue;
+    }
+    P.pcnt[i] = cnt;
+    P.pbase[i] = (int)foff;
+    P.flen[i] = L + 2 * (cnt - 1);
+    st_splits += cnt - 1;
+  }
+  st_splits = __reduce_add_sync(0xffffffffu, st_splits);
+  if ((threadIdx.x & 31) == 0 && st_splits)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)st_splits);
+}
+
+cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
+                              const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                              const LongList& D1, Counters* C, int sms, cudaStream_t s) {
+  k_repair_one<<<sms * 8, kBlock, 0, s>>>(M, lab, tf, succ, P, F, pool, D1, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
+                                const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                                const LongList& Dm, Counters* C, int sms, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_repair_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kRsSmem);
+    attr = true;
+  }
+  const int per_sm = (int)((220 * 1024) / (kRsSmem + 1024));
+  const int grid = sms * (per_sm < 1 ? 1 : per_sm);
+  k_repair_multi<<<grid, kRsThreads, kRsSmem, s>>>(M, lab, tf, succ, P, F, pool, Dm, C);
+  return cudaGetLastError();
+}
+
+}  // namespace polylla
