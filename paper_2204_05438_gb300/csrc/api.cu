@@ -39,7 +39,8 @@ struct polylla_mesh {
 
   uint8_t* lab = nullptr;
   int* seeds = nullptr;
-  int* succ = nullptr;    // boundary successor of every frontier half-edge
+  int* entry = nullptr;   // per seed: entry half-edge of its region (or -1 - t)
+  int* succ = nullptr;    // per frontier half-edge: boundary successor | tip flag
   int* tf = nullptr;      // twin | frontier bit, per half-edge (written by the label phase)
   int* visit = nullptr;   // per triangle: search stamp of the long-polygon blocks
   int* loc = nullptr;     // per half-edge: member index inside a long-polygon block
@@ -58,6 +59,11 @@ struct polylla_mesh {
   long long* off_final = nullptr;
   int* vtx_final = nullptr;
   Counters* C = nullptr;
+
+  // the three kernels after the walk touch disjoint polygons: fork to two side
+  // streams and join back (sequential in timing mode, for per-kernel times)
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 
   bool timing = false;
   std::vector<TimingRec> recs;
@@ -129,7 +135,7 @@ void free_all(polylla_mesh* h) {
                   h->P.pos,    h->F.pos,     h->F.len,     h->F.h,        h->pool.v,
                   h->tile_sum, h->tile_off,  h->off_trav,  h->vtx_trav,   h->off_final,
                   h->vtx_final, h->C,         h->Dl.poly,   h->P.tip_h,
-                  h->Dm.poly};
+                  h->Dm.poly,   h->entry};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_inputs) {
@@ -142,10 +148,22 @@ void free_all(polylla_mesh* h) {
     cudaEventDestroy(r.b);
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k) {
+    if (h->side[k]) cudaStreamDestroy(h->side[k]);
+    if (h->join[k]) cudaEventDestroy(h->join[k]);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
 }
 
 polylla_status alloc_derived(polylla_mesh* h) {
   const long long m = h->M.m, n = h->M.n;
+  for (int k = 0; k < 2; ++k) {
+    if (cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join[k], cudaEventDisableTiming) != cudaSuccess)
+      return POLYLLA_ERR_CUDA;
+  }
+  if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess)
+    return POLYLLA_ERR_CUDA;
   const long long ntiles_tri = (m + kTriTile - 1) / kTriTile;
   const long long ntiles_poly = (m + kPolyTile - 1) / kPolyTile;
   const long long ntiles = ntiles_tri > ntiles_poly ? ntiles_tri : ntiles_poly;
@@ -162,6 +180,7 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->lab, m + 4);
   ALLOC(h->seeds, m);
   ALLOC(h->succ, 3 * m);
+  ALLOC(h->entry, m);
   ALLOC(h->tf, 3 * m);
   ALLOC(h->visit, m);
   ALLOC(h->loc, 3 * m);
@@ -243,7 +262,7 @@ polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
   }));
   const int g = grid_for(h, M.m, kTriTile);
   POLY_TRY(launch(h, "seed_write", s,
-                  [&] { return launch_seed_write(h->lab, M.m, h->tile_off, h->seeds, g, s); }));
+                  [&] { return launch_seed_write(h->lab, M.m, h->tile_off, h->seeds, h->entry, g, s); }));
   h->phase = kSeeded;
   return POLYLLA_OK;
 }
@@ -262,23 +281,39 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   }
   const int gw = grid_for(h, M.m, 4 * 256);
   POLY_TRY(launch(h, "walk", s, [&] {
-    return launch_walk(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg, h->Dl,
-                       h->Dm, repair, h->C, gw, s);
+    return launch_walk(M, h->tf, h->entry, h->succ, h->P, h->pool, h->Lg, h->Dl, h->Dm, repair,
+                       h->C, gw, s);
+  }));
+  // repair_one (this stream), repair_multi and long (side streams) at once
+  const bool fork = !h->timing;
+  cudaStream_t s1 = s, s2 = s;
+  if (fork) {
+    POLY_TRY(cuda_status(cudaEventRecord(h->fork, s)));
+    for (int k = 0; k < 2; ++k)
+      POLY_TRY(cuda_status(cudaStreamWaitEvent(h->side[k], h->fork, 0)));
+    s1 = h->side[0];
+    s2 = h->side[1];
+  }
+  POLY_TRY(launch(h, "long", s1, [&] {
+    return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg, h->visit,
+                       h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->C, 2 * h->sms, s1);
   }));
   if (repair) {
+    POLY_TRY(launch(h, "repair_multi", s2, [&] {
+      return launch_repair_multi(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dm, h->C,
+                                 h->sms, s2);
+    }));
     POLY_TRY(launch(h, "repair_one", s, [&] {
       return launch_repair_one(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dl, h->C,
                                h->sms, s);
     }));
-    POLY_TRY(launch(h, "repair_multi", s, [&] {
-      return launch_repair_multi(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dm, h->C,
-                                 h->sms, s);
-    }));
   }
-  POLY_TRY(launch(h, "long", s, [&] {
-    return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg, h->visit,
-                       h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->C, 2 * h->sms, s);
-  }));
+  if (fork) {
+    for (int k = 0; k < 2; ++k) {
+      POLY_TRY(cuda_status(cudaEventRecord(h->join[k], h->side[k])));
+      POLY_TRY(cuda_status(cudaStreamWaitEvent(s, h->join[k], 0)));
+    }
+  }
   const int gt = grid_for(h, M.m, kPolyTile);
   POLY_TRY(launch(h, "out_tiles", s,
                   [&] { return launch_final_tiles(h->P, h->tile_sum, h->C, gt, s); }));

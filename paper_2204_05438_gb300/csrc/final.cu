@@ -40,75 +40,83 @@ cudaError_t launch_final_tiles(const PolyArrays& P, long long* tile_sum, Counter
   return cudaGetLastError();
 }
 
-// The unsplit polygons of a warp are copied together: the warp's 32 copy jobs are
-// laid end to end and each lane moves every 32nd element, so reads and writes are
-// coalesced (the 32 polygons of a warp were also pooled contiguously by k_walk).
-// Split polygons' pieces are copied by their own thread.
+// Every polygon's output -- its pieces in order, for a split one -- lies in one
+// contiguous stretch of the pool, and the untouched polygons that one walk warp
+// pooled (32 consecutive seeds) lie back to back.  So a warp's 32 polygons form a
+// few runs that are contiguous both in the pool and in the output, broken where
+// a polygon was split or walked elsewhere; each run is copied by the whole warp,
+// coalesced.  Piece offsets are written by the polygon's own thread.
 __global__ void __launch_bounds__(kBlock) k_final_write(PolyArrays P, FinalPieces F, Pool pool,
                                                         const long long* __restrict__ tile_off,
                                                         long long* __restrict__ off,
                                                         int* __restrict__ vtx, long long m,
                                                         Counters* C) {
   __shared__ long long sh[kBlock / 32];
-  __shared__ int s_incl[kBlock];
-  __shared__ long long s_src[kBlock], s_dst[kBlock];
+  __shared__ unsigned long long shu[kBlock / 32];
   const long long n = C->n_seeds;
   const long long ntiles = (n + kPolyTile - 1) / kPolyTile;
   const int lane = threadIdx.x & 31;
-  const int wbase = threadIdx.x & ~31;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long i = tile * kPolyTile + threadIdx.x;
     long long c = 0, l = 0;
     if (i < n) out_counts(P, i, &c, &l);
-    long long t0, t1;
-    const long long pb = tile_off[2 * tile] + block_exclusive_scan(c, &t0, sh);
-    const long long vb = tile_off[2 * tile + 1] + block_exclusive_scan(l, &t1, sh);
+    // one scan of (count << 40) + length, exact while every polygon of the tile has
+    // fewer than 2^16 pieces (then the tile has fewer than 2^24; it always has
+    // fewer than 2^40 vertices); otherwise two scans
+    long long pb, vb;
+    if (!__syncthreads_or(c >= (1ll << 16))) {
+      unsigned long long t0;
+      const unsigned long long x = block_exclusive_scan(
+          ((unsigned long long)c << 40) + (unsigned long long)l, &t0, shu);
+      pb = tile_off[2 * tile] + (long long)(x >> 40);
+      vb = tile_off[2 * tile + 1] + (long long)(x & ((1ull << 40) - 1));
+    } else {
+      long long t0, t1;
+      pb = tile_off[2 * tile] + block_exclusive_scan(c, &t0, sh);
+      vb = tile_off[2 * tile + 1] + block_exclusive_scan(l, &t1, sh);
+    }
     bool ok = i < n;
     if (ok && (pb + c > m || vb + l > 3 * m)) {
       set_error(C, POLYLLA_ERR_LIMIT, 80);
       ok = false;
     }
-    const int pc = ok ? P.pcnt[i] : 0;
-    // unsplit polygons: one offset, and a copy job for the warp
-    int mine = 0;
-    if (ok && pc == 0) {
-      off[pb] = vb;
-      mine = (int)l;
-      s_src[threadIdx.x] = P.pos[i];
-      s_dst[threadIdx.x] = vb;
-    }
-    int incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += y;
-    }
-    s_incl[threadIdx.x] = incl;
-    __syncwarp();
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    for (int k = lane; k < total; k += 32) {
-      int lo = 0, hi = 31;  // first lane whose inclusive sum exceeds k
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (s_incl[wbase + mid] > k) hi = mid;
-        else lo = mid + 1;
+    long long src = -1;
+    if (ok) {
+      const int pc = P.pcnt[i];
+      if (pc == 0) {
+        src = P.pos[i];
+        off[pb] = vb;
+      } else {
+        const long long fb = P.pbase[i];
+        src = F.pos[fb];
+        long long acc = 0;
+        for (int r = 0; r < pc; ++r) {
+          off[pb + r] = vb + acc;
+          acc += F.len[fb + r];
+        }
       }
-      const int excl = lo ? s_incl[wbase + lo - 1] : 0;
-      const int rel = k - excl;
-      vtx[s_dst[wbase + lo] + rel] = pool.v[s_src[wbase + lo] + rel];
-    }
-    __syncwarp();
-    // split polygons: offsets and pieces by their own thread
-    if (ok && pc > 0) {
-      long long acc = 0;
-      const long long fb = P.pbase[i];
-      for (int r = 0; r < pc; ++r) {
-        const int len = F.len[fb + r];
-        off[pb + r] = vb + acc;
-        const int* src = pool.v + F.pos[fb + r];
-        for (int q = 0; q < len; ++q) vtx[vb + acc + q] = src[q];
-        acc += len;
+      if (src < 0 || src + l > pool.cap) {
+        set_error(C, POLYLLA_ERR_LIMIT, 81);
+        src = -1;
       }
+    }
+    const unsigned um = __ballot_sync(0xffffffffu, src >= 0);
+    const long long prev_end = __shfl_up_sync(0xffffffffu, src + l, 1);
+    const bool first = src >= 0 && (lane == 0 || !((um >> (lane - 1)) & 1u) || prev_end != src);
+    unsigned starts = __ballot_sync(0xffffffffu, first);
+    const unsigned breaks = starts | ~um;
+    while (starts) {
+      const int a = __ffs(starts) - 1;
+      starts &= starts - 1;
+      const unsigned above = breaks & ~((2u << a) - 1u);
+      const int e = above ? __ffs(above) - 1 : 32;
+      const long long s0 = __shfl_sync(0xffffffffu, src, a);
+      const long long d0 = __shfl_sync(0xffffffffu, vb, a);
+      const long long s1 = __shfl_sync(0xffffffffu, src + l, e - 1);
+      const long long run = s1 - s0;
+      const int* from = pool.v + s0;
+      int* to = vtx + d0;
+      for (long long k = lane; k < run; k += 32) to[k] = from[k];
     }
   }
 }

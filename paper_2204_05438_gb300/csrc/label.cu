@@ -246,9 +246,13 @@ cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_s
 }
 
 // ------------------------------------------------------------------ seed compaction
+// With `entry` non-null, also the entry half-edge of each seed's region for the
+// walk: 3t + k for the first frontier edge k of t (label bits 2-4), or -1 - t when
+// t has no frontier edge (the walk then turns around t's first vertex).
 __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict__ lab, long long m,
                                                        const long long* __restrict__ tile_off,
-                                                       int* __restrict__ seeds) {
+                                                       int* __restrict__ seeds,
+                                                       int* __restrict__ entry) {
   __shared__ int sh[kBlock / 32];
   const long long ntiles = (m + kTriTile - 1) / kTriTile;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -267,14 +271,24 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
     const long long base = tile_off[2 * tile] + pos;
     int w = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if ((own >> (8 * j + 5)) & 1) seeds[base + w++] = (int)(t0 + j);
+    for (int j = 0; j < 4; ++j) {
+      const unsigned b = own >> (8 * j);
+      if ((b >> 5) & 1) {
+        const int t = (int)(t0 + j);
+        seeds[base + w] = t;
+        if (entry) {
+          const unsigned fr = (b >> 2) & 7u;
+          entry[base + w] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
+        }
+        ++w;
+      }
+    }
   }
 }
 
 cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
-                              int* seeds, int grid, cudaStream_t s) {
-  k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, tile_off, seeds);
+                              int* seeds, int* entry, int grid, cudaStream_t s) {
+  k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, tile_off, seeds, entry);
   return cudaGetLastError();
 }
 

@@ -114,7 +114,7 @@ extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64
                           reinterpret_cast<long long*>(d_n_seeds), &C->scratch0, nullptr, 0, 0, C,
                           s);
   if (e == cudaSuccess)
-    e = launch_seed_write(d_lab, n_tri, tile_off, d_seeds, grid_of(sms, n_tri, kTriTile), s);
+    e = launch_seed_write(d_lab, n_tri, tile_off, d_seeds, nullptr, grid_of(sms, n_tri, kTriTile), s);
   int err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &C->error, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -18,6 +18,8 @@ namespace polylla {
 constexpr int kBlock = 256;                    // threads per block, every kernel
 constexpr int kTriPerThread = 4;               // label kernels: 4 triangles = 3 x int4
 constexpr int kTriTile = kBlock * kTriPerThread;  // 1024 triangles per seed-count tile
+constexpr int kWalkThreads = 256;  // k_walk block
+constexpr int kWalkCap = 64;       // longer polygons go to one thread block each (long.cu)
 constexpr int kPolyTile = kBlock;              // per-polygon scans: one polygon per thread
 constexpr int kScanThreads = 1024;
 
@@ -115,7 +117,7 @@ cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int gr
 cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, int* tf,
                                Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
-                              int* seeds, int grid, cudaStream_t s);
+                              int* seeds, int* entry, int grid, cudaStream_t s);
 // Exclusive scan of per-tile pairs.  Tile count = ceil(n / tile) with n = *n_dev if
 // n_dev, else n_host.  Totals go to *tot0, *tot1.  end_mode 1: end[n] = total0;
 // end_mode 2: end[total0] = total1 (index checked against end_cap).
@@ -144,9 +146,10 @@ struct FinalPieces {
   long long cap;
 };
 
-// Vertex pool: every output polygon is written here first, in its final order,
-// by the thread (or block) that walked it; the CSR is a copy.  Capacity 6m + 2n:
-// the output (at most 3m + 2n) plus staging for one-tip polygons (at most 3m).
+// Vertex pool: every output polygon is written here first, in its final order and
+// contiguously (a split polygon's pieces back to back), by the thread or block
+// that walked or split it; the CSR is a copy.  Capacity 6m + 2n: the output (at
+// most 3m + 2n) and the staging of one-tip polygons (at most 3m).
 struct Pool {
   int* v;
   long long cap;
@@ -161,10 +164,10 @@ struct LongList {
 cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
                         cudaStream_t s);
 // One thread per seed: walk (<= kWalkCap) and, if `repair`, split the polygon.
-cudaError_t launch_walk(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
-                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                        const LongList& Lg, const LongList& D1, const LongList& Dm, int repair,
-                        Counters* C, int grid, cudaStream_t s);
+cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
+                        const PolyArrays& P, const Pool& pool, const LongList& Lg,
+                        const LongList& D1, const LongList& Dm, int repair, Counters* C, int grid,
+                        cudaStream_t s);
 // One thread per polygon with one tip / with several tips (listed by k_walk).
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,

@@ -5,11 +5,12 @@
 //           frontier half-edge of its region's boundary (PolyConstruction's
 //           turn), with the barrier-edge tip flag.  The three turns of a triangle
 //           advance together so their loads overlap.
-//   k_walk  one thread per seed: enter the region, chase succ around the cycle
-//           (at most kWalkCap vertices, staged in shared memory), note the
-//           canonical start and the tips.  A polygon without tips (or any, when no
-//           reparation is asked for) is copied, rotated to its canonical start,
-//           into the vertex pool, whose space is handed out per warp.  A polygon
+//   k_walk  one thread per seed: enter the region (at the entry half-edge the
+//           seed kernel found), chase succ around the cycle (at most kWalkCap
+//           vertices, staged in shared memory), note the canonical start and the
+//           tips.  A polygon without tips (or any, when no reparation is asked
+//           for) is copied, rotated to its canonical start, into the vertex pool,
+//           whose space is handed out per warp.  A polygon
 //           with tips is listed -- one tip (about 90% of them) or several -- so
 //           that the dependent loads of a split do not stall the 31 other lanes of
 //           its warp; a longer one is left to one thread block (long.cu).
@@ -96,14 +97,12 @@ __device__ __forceinline__ long long warp_alloc(long long* counter, int need) {
   return (long long)base + incl - need;
 }
 
-constexpr int kWalkThreads = 256;
 
-__global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, uint8_t* lab, int* tf,
-                                                       const int* __restrict__ seeds,
+__global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
+                                                       const int* __restrict__ entry,
                                                        const int* __restrict__ succ, PolyArrays P,
-                                                       FinalPieces F, Pool pool, LongList Lg,
-                                                       LongList D1, LongList Dm, int repair,
-                                                       Counters* C) {
+                                                       Pool pool, LongList Lg, LongList D1,
+                                                       LongList Dm, int repair, Counters* C) {
   extern __shared__ int sbuf[];
   int* my = sbuf + threadIdx.x * kWalkCap;
   const long long n = C->n_seeds;
@@ -116,7 +115,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, uint8_t* lab, 
     int len = 0, ntips = 0, tip_h = -1, rank0 = 0, start = 0;
     bool closed = false, is_long = false;
     if (i < n) {
-      const int e = region_entry_tf(tf, seeds[i], H, limit);
+      int e = entry[i];
+      if (e < 0) e = region_entry_tf(tf, -1 - e, H, limit);
       if (e < 0) {
         set_error(C, POLYLLA_ERR_LIMIT, 51);
       } else {
@@ -214,18 +214,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, uint8_t* lab, 
   }
 }
 
-cudaError_t launch_walk(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
-                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                        const LongList& Lg, const LongList& D1, const LongList& Dm, int repair,
-                        Counters* C, int grid, cudaStream_t s) {
+cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
+                        const PolyArrays& P, const Pool& pool, const LongList& Lg,
+                        const LongList& D1, const LongList& Dm, int repair, Counters* C, int grid,
+                        cudaStream_t s) {
   const size_t smem = sizeof(int) * (size_t)kWalkThreads * kWalkCap;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_walk<<<grid, kWalkThreads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, D1, Dm, repair,
-                                          C);
+  k_walk<<<grid, kWalkThreads, smem, s>>>(M, tf, entry, succ, P, pool, Lg, D1, Dm, repair, C);
   return cudaGetLastError();
 }
 

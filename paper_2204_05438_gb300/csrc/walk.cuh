@@ -23,7 +23,6 @@ namespace polylla {
 
 constexpr int kTipFlag = 1 << 31;
 constexpr int kSuccMask = 0x7fffffff;
-constexpr int kWalkCap = 64;  // longer polygons go to one thread block each (long.cu)
 
 __device__ __forceinline__ int tf_twin(int x) { return x & 0x7fffffff; }
 
