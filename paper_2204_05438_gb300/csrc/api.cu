@@ -42,7 +42,6 @@ struct polylla_mesh {
   int* entry = nullptr;   // per seed: entry half-edge of its region (or -1 - t)
   int* succ = nullptr;    // per frontier half-edge: boundary successor | tip flag
   int* tf = nullptr;      // twin | frontier bit, per half-edge (written by the label phase)
-  int* visit = nullptr;   // per triangle: search stamp of the long-polygon blocks
   int* loc = nullptr;     // per half-edge: member index inside a long-polygon block
   int* vstamp = nullptr;  // per vertex: "endpoint of a split edge" stamp
   LongList Lg{};
@@ -129,7 +128,7 @@ cudaError_t dalloc(T** p, long long count) {
 }
 
 void free_all(polylla_mesh* h) {
-  void* ptrs[] = {h->lab,      h->seeds,     h->succ,      h->tf,         h->visit,
+  void* ptrs[] = {h->lab,      h->seeds,     h->succ,      h->tf,
                   h->loc,      h->vstamp,    h->Lg.poly,   h->P.start,    h->P.len,
                   h->P.ntip,   h->P.mode,    h->P.pcnt,    h->P.pbase,    h->P.flen,
                   h->P.pos,    h->F.pos,     h->F.len,     h->F.h,        h->pool.v,
@@ -182,7 +181,6 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->succ, 3 * m);
   ALLOC(h->entry, m);
   ALLOC(h->tf, 3 * m);
-  ALLOC(h->visit, m);
   ALLOC(h->loc, 3 * m);
   ALLOC(h->vstamp, n);
   ALLOC(h->Lg.poly, m);
@@ -211,7 +209,6 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->C, 1);
 #undef ALLOC
   // stamped arrays start empty (run stamps are never 0)
-  if (e == cudaSuccess) e = cudaMemset(h->visit, 0, sizeof(int) * (size_t)m);
   if (e == cudaSuccess) e = cudaMemset(h->vstamp, 0, sizeof(int) * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(h->C, 0, sizeof(Counters));
   return cuda_status(e);
@@ -237,7 +234,6 @@ polylla_status check_handle(polylla_mesh* h) {
 polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   const DevMesh& M = h->M;
   if (h->epoch >= 0x3ffffff0) {  // stamps: wrap around once in 2^30 runs
-    POLY_TRY(cuda_status(cudaMemsetAsync(h->visit, 0, sizeof(int) * (size_t)M.m, s)));
     POLY_TRY(cuda_status(cudaMemsetAsync(h->vstamp, 0, sizeof(int) * (size_t)M.n, s)));
     h->epoch = 0;
   }
@@ -295,7 +291,7 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
     s2 = h->side[1];
   }
   POLY_TRY(launch(h, "long", s1, [&] {
-    return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg, h->visit,
+    return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg,
                        h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->C, 2 * h->sms, s1);
   }));
   if (repair) {

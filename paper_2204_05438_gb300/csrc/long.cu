@@ -5,9 +5,10 @@
 // load at a time would make each of them the critical path of the run.  A block:
 //
 //   1. collects the region's frontier half-edges by a breadth-first search over
-//      its triangles across non-frontier edges (tf words).  Every triangle reaches
-//      its seed through its longest-edge links, so the search from the seed ends
-//      after at most (longest-edge propagation depth + 1) levels;
+//      its triangles across non-frontier edges (tf words), with the visited set in
+//      a shared-memory hash table.  Every triangle reaches its seed through its
+//      longest-edge links, so the search from the seed ends after at most
+//      (longest-edge propagation depth + 1) levels;
 //   2. maps each half-edge's successor to a member index, finds the canonical
 //      start by a block reduction;
 //   3. without reparation (or tips): ranks the cycle from its start by pointer
@@ -34,6 +35,22 @@ constexpr int kLongThreads = 512;
 constexpr int kLM = 4096;  // members of one long polygon (with its split half-edges)
 constexpr int kLT = 4096;  // BFS queue: triangles of one long region
 constexpr int kLongSmemInts = kLT + 10 * kLM;
+constexpr int kHashBits = 13;  // visited-triangle table of the search: 2 * kLM slots
+constexpr int kHashSlots = 1 << kHashBits;
+static_assert(kHashSlots == 2 * kLM, "the table spans two member buffers");
+
+// Insert triangle t into the block's visited table (open addressing, -1 = empty).
+// Returns 1 if t was new, 0 if it was there, -1 if the table is full.
+__device__ __forceinline__ int visit_insert(int* tab, int t) {
+  unsigned slot = ((unsigned)t * 2654435761u) >> (32 - kHashBits);
+  for (int probe = 0; probe < kHashSlots; ++probe) {
+    const int old = atomicCAS(tab + slot, -1, t);
+    if (old == -1) return 1;
+    if (old == t) return 0;
+    slot = (slot + 1) & (kHashSlots - 1);
+  }
+  return -1;
+}
 
 __device__ void block_min_key(unsigned long long key, int idx, unsigned long long* s_key,
                               int* s_idx, unsigned long long* out_key, int* out_idx) {
@@ -184,7 +201,6 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
                                                        const int* __restrict__ seeds,
                                                        const int* __restrict__ succ, PolyArrays P,
                                                        FinalPieces F, Pool pool, LongList Lg,
-                                                       int* __restrict__ visit,
                                                        int* __restrict__ loc,
                                                        int* __restrict__ vstamp, int epoch,
                                                        int repair, Counters* C) {
@@ -211,13 +227,16 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
     const long long i = Lg.poly[j];
     const int t0 = seeds[i];
     // ---- 1. breadth-first search of the region
+    int* vis = R0;  // R0..R1: the visited table
+    for (int q = threadIdx.x; q < kHashSlots; q += blockDim.x) vis[q] = -1;
+    __syncthreads();
     if (threadIdx.x == 0) {
       s_head = 0;
       s_tail = 1;
       s_nm = 0;
       s_over = 0;
       RQ[0] = t0;
-      visit[t0] = epoch;
+      visit_insert(vis, t0);
     }
     __syncthreads();
     for (;;) {
@@ -237,10 +256,13 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
             s_over = 2;
           } else {
             const int nb = x / 3;
-            if (atomicExch(visit + nb, epoch) != epoch) {
+            const int ins = visit_insert(vis, nb);
+            if (ins > 0) {
               const int p = atomicAdd(&s_tail, 1);
               if (p < kLT) RQ[p] = nb;
               else s_over = 1;
+            } else if (ins < 0) {
+              s_over = 1;
             }
           }
         }
@@ -348,35 +370,55 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
     //          a split tip with a smaller id ends its split edge on it
     int* sb = R8;          // tip vertices, sorted
     int* st = R8 + 2048;   // their tip indices (nt <= kLM / 2)
-    if (threadIdx.x == 0) {
-      int ns = 0;
-      if (!s_fail && 2 * nt <= kLM) {
-        for (int t = 0; t < nt; ++t) {
-          sb[t] = tip_b[t];
-          st[t] = t;
-        }
-        heap_sort(sb, st, nt);
-        int* cancelled = R1;
-        for (int t = 0; t < nt; ++t) cancelled[t] = 0;
-        for (int q = 0; q < nt; ++q) {
-          const int t = st[q];
-          if (cancelled[t]) continue;
-          RQ[ns++] = t;  // chord list, increasing tip vertex
-          const int x = tip_x[t];
-          if (x > sb[q]) {  // a larger tip at x is removed by this split edge
-            int lo = q + 1, hi = nt - 1;
-            while (lo <= hi) {
-              const int mid = (lo + hi) >> 1;
-              if (sb[mid] < x) {
-                lo = mid + 1;
-              } else if (sb[mid] > x) {
-                hi = mid - 1;
-              } else {
-                cancelled[st[mid]] = 1;
-                break;
-              }
+    int* cx = R2;          // sorted index of the larger tip at each split edge's end
+    int* cancelled = R1;
+    const bool sortable = !s_fail && 2 * nt <= kLM;
+    if (sortable && nt <= 1024) {
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) {  // rank by counting
+        const int b = tip_b[t];
+        int r = 0;
+        for (int u = 0; u < nt; ++u) r += tip_b[u] < b;
+        sb[r] = b;
+        st[r] = t;
+      }
+    } else if (sortable && threadIdx.x == 0) {
+      for (int t = 0; t < nt; ++t) {
+        sb[t] = tip_b[t];
+        st[t] = t;
+      }
+      heap_sort(sb, st, nt);
+    }
+    __syncthreads();
+    if (sortable) {
+      for (int q = threadIdx.x; q < nt; q += blockDim.x) {
+        cancelled[q] = 0;
+        const int x = tip_x[st[q]];
+        int hit = -1;
+        if (x > sb[q]) {
+          int lo = q + 1, hi = nt - 1;
+          while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sb[mid] < x) {
+              lo = mid + 1;
+            } else if (sb[mid] > x) {
+              hi = mid - 1;
+            } else {
+              hit = mid;
+              break;
             }
           }
+        }
+        cx[q] = hit;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ns = 0;
+      if (sortable) {
+        for (int q = 0; q < nt; ++q) {
+          if (cancelled[q]) continue;
+          RQ[ns++] = st[q];  // chord list, increasing tip vertex
+          if (cx[q] >= 0) cancelled[cx[q]] = 1;
         }
       } else {
         s_fail = 1;
@@ -567,7 +609,7 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
 
 cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                        const LongList& Lg, int* visit, int* loc, int* vstamp, int epoch,
+                        const LongList& Lg, int* loc, int* vstamp, int epoch,
                         int repair, Counters* C, int grid, cudaStream_t s) {
   const size_t smem = sizeof(int) * (size_t)kLongSmemInts;
   static bool attr = false;
@@ -575,7 +617,7 @@ cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seed
     cudaFuncSetAttribute(k_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_long<<<grid, kLongThreads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, visit, loc,
+  k_long<<<grid, kLongThreads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, loc,
                                           vstamp, epoch, repair, C);
   return cudaGetLastError();
 }

@@ -178,7 +178,7 @@ cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const i
 // One block per long polygon: gather, rank and, if `repair`, split.
 cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                        const LongList& Lg, int* visit, int* loc, int* vstamp, int epoch,
+                        const LongList& Lg, int* loc, int* vstamp, int epoch,
                         int repair, Counters* C, int grid, cudaStream_t s);
 // Output: per-tile (polygon count, vertex count); then offsets and the copy.
 cudaError_t launch_final_tiles(const PolyArrays& P, long long* tile_sum, Counters* C, int grid,
