@@ -18,7 +18,8 @@
  *                   positive area.  Half-edge h = 3t+k runs from tri[h] to
  *                   tri[3t+(k+1)%3].
  *   twin int32[3m]  device; the opposite half-edge of h, or -1 on the border.
- * Sizes: 3 <= n < 2^31, 1 <= m <= 700,000,000 (half-edge ids fit int32).
+ * Sizes: 3 <= n < 2^30, 1 <= m < 2^29 (half-edge ids fit int32; the output scan
+ * packs a polygon count and a vertex count in one 64-bit word).
  *
  * Ownership: the input arrays are borrowed, never written, and must stay valid
  * until polylla_mesh_destroy.  Every derived array (labels, seeds, polygons) is

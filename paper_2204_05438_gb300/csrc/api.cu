@@ -253,12 +253,13 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
 polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
   const DevMesh& M = h->M;
   POLY_TRY(launch(h, "scan_seeds", s, [&] {
-    return launch_scan_tiles(h->tile_sum, h->tile_off, M.m, nullptr, kTriTile, &h->C->n_seeds,
-                             &h->C->scratch0, nullptr, 0, 0, h->C, s);
+    return launch_scan_tiles(h->tile_sum, h->tile_off, M.m, nullptr, M.m, kTriTile,
+                             &h->C->n_seeds, &h->C->scratch0, nullptr, 0, 0, h->C, s);
   }));
   const int g = grid_for(h, M.m, kTriTile);
-  POLY_TRY(launch(h, "seed_write", s,
-                  [&] { return launch_seed_write(h->lab, M.m, h->tile_off, h->seeds, h->entry, g, s); }));
+  POLY_TRY(launch(h, "seed_write", s, [&] {
+    return launch_seed_write(h->lab, M.m, h->tile_off, h->seeds, h->entry, g, s);
+  }));
   h->phase = kSeeded;
   return POLYLLA_OK;
 }
@@ -310,15 +311,15 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
       POLY_TRY(cuda_status(cudaStreamWaitEvent(s, h->join[k], 0)));
     }
   }
+  // one pass: offsets by look-back (status words zeroed; the ticket counter was
+  // reset with the pass's counters)
   const int gt = grid_for(h, M.m, kPolyTile);
-  POLY_TRY(launch(h, "out_tiles", s,
-                  [&] { return launch_final_tiles(h->P, h->tile_sum, h->C, gt, s); }));
-  POLY_TRY(launch(h, "out_scan", s, [&] {
-    return launch_scan_tiles(h->tile_sum, h->tile_off, 0, &h->C->n_seeds, kPolyTile,
-                             &h->C->n_poly, &h->C->n_vtx, off, 2, M.m, h->C, s);
-  }));
+  const long long ntiles = (M.m + kPolyTile - 1) / kPolyTile;
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(h->tile_sum);
+  POLY_TRY(cuda_status(
+      cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)ntiles, s)));
   return launch(h, "out_write", s, [&] {
-    return launch_final_write(h->P, h->F, h->pool, h->tile_off, off, vtx, M.m, h->C, gt, s);
+    return launch_final_write(h->P, h->F, h->pool, status, off, vtx, M.m, h->C, gt, s);
   });
 }
 
@@ -375,7 +376,7 @@ polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, cons
   if (!out) return POLYLLA_ERR_INVALID_ARG;
   *out = nullptr;
   if (!d_xy || !d_tri || !d_twin) return POLYLLA_ERR_INVALID_ARG;
-  if (n_vertices < 3 || n_vertices > 0x7fffffffll || n_tri < 1 || n_tri > 700000000ll)
+  if (n_vertices < 3 || n_vertices >= kMaxVertices || n_tri < 1 || n_tri >= kMaxTriangles)
     return POLYLLA_ERR_INVALID_ARG;
   if ((flags & ~POLYLLA_VALIDATE) != 0) return POLYLLA_ERR_INVALID_ARG;
   if (((uintptr_t)d_xy | (uintptr_t)d_tri | (uintptr_t)d_twin) & 15u) return POLYLLA_ERR_INVALID_ARG;
@@ -399,7 +400,7 @@ polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, cons
 polylla_status polylla_mesh_create_host(int64_t n_vertices, int64_t n_tri, polylla_mesh_t* out) {
   if (!out) return POLYLLA_ERR_INVALID_ARG;
   *out = nullptr;
-  if (n_vertices < 3 || n_vertices > 0x7fffffffll || n_tri < 1 || n_tri > 700000000ll)
+  if (n_vertices < 3 || n_vertices >= kMaxVertices || n_tri < 1 || n_tri >= kMaxTriangles)
     return POLYLLA_ERR_INVALID_ARG;
   polylla_mesh* h = new (std::nothrow) polylla_mesh();
   if (!h) return POLYLLA_ERR_OOM;

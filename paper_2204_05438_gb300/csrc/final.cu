@@ -2,9 +2,9 @@
 // polygon already sits in the vertex pool in its final vertex order (written by
 // the thread or block that walked it); the order of the polygons is fixed here:
 // traversal polygons in seed order, each split polygon replaced in place by its
-// pieces.  One scan over the polygons' (piece count, vertex count) replaces the
-// paper's AtomicAdd on i_Gmesh / i_Gpos, then each polygon's pieces are copied to
-// their offsets.
+// pieces.  One single-pass scan over the polygons' (piece count, vertex count)
+// replaces the paper's AtomicAdd on i_Gmesh / i_Gpos, and each polygon's pieces
+// are copied to their offsets in the same pass.
 #include "polylla_internal.cuh"
 
 namespace polylla {
@@ -16,64 +16,73 @@ __device__ __forceinline__ void out_counts(const PolyArrays& P, long long i, lon
   *l = P.flen[i];
 }
 
-__global__ void __launch_bounds__(kBlock) k_final_tiles(PolyArrays P, long long* __restrict__ tile_sum,
-                                                        Counters* C) {
-  __shared__ long long sh[kBlock / 32];
-  const long long n = C->n_seeds;
-  const long long ntiles = (n + kPolyTile - 1) / kPolyTile;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long i = tile * kPolyTile + threadIdx.x;
-    long long c = 0, l = 0;
-    if (i < n) out_counts(P, i, &c, &l);
-    const long long s0 = block_sum(c, sh);
-    const long long s1 = block_sum(l, sh);
-    if (threadIdx.x == 0) {
-      tile_sum[2 * tile] = s0;
-      tile_sum[2 * tile + 1] = s1;
-    }
-  }
-}
-
-cudaError_t launch_final_tiles(const PolyArrays& P, long long* tile_sum, Counters* C, int grid,
-                               cudaStream_t s) {
-  k_final_tiles<<<grid, kBlock, 0, s>>>(P, tile_sum, C);
-  return cudaGetLastError();
-}
-
 // Every polygon's output -- its pieces in order, for a split one -- lies in one
 // contiguous stretch of the pool, and the untouched polygons that one walk warp
 // pooled (32 consecutive seeds) lie back to back.  So a warp's 32 polygons form a
 // few runs that are contiguous both in the pool and in the output, broken where
 // a polygon was split or walked elsewhere; each run is copied by the whole warp,
 // coalesced.  Piece offsets are written by the polygon's own thread.
+//
+// The tile offsets come from a look-back over `status` in the same pass (tiles in
+// ticket order; one word per tile packs the piece count << 33 | vertex count,
+// exact within the mesh size limits), and the last tile writes the totals and the
+// CSR end marker.
 __global__ void __launch_bounds__(kBlock) k_final_write(PolyArrays P, FinalPieces F, Pool pool,
-                                                        const long long* __restrict__ tile_off,
+                                                        unsigned long long* status,
                                                         long long* __restrict__ off,
                                                         int* __restrict__ vtx, long long m,
                                                         Counters* C) {
   __shared__ long long sh[kBlock / 32];
   __shared__ unsigned long long shu[kBlock / 32];
+  __shared__ long long s_tile, s_p, s_v;
   const long long n = C->n_seeds;
   const long long ntiles = (n + kPolyTile - 1) / kPolyTile;
   const int lane = threadIdx.x & 31;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (;;) {
+    if (threadIdx.x == 0)
+      s_tile = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->ticket), 1ull);
+    __syncthreads();
+    const long long tile = s_tile;
+    __syncthreads();
+    if (tile >= ntiles) break;
     const long long i = tile * kPolyTile + threadIdx.x;
     long long c = 0, l = 0;
     if (i < n) out_counts(P, i, &c, &l);
     // one scan of (count << 40) + length, exact while every polygon of the tile has
     // fewer than 2^16 pieces (then the tile has fewer than 2^24; it always has
     // fewer than 2^40 vertices); otherwise two scans
-    long long pb, vb;
+    long long pl, vl, tc, tl;  // in-tile exclusive offsets and tile totals
     if (!__syncthreads_or(c >= (1ll << 16))) {
       unsigned long long t0;
       const unsigned long long x = block_exclusive_scan(
           ((unsigned long long)c << 40) + (unsigned long long)l, &t0, shu);
-      pb = tile_off[2 * tile] + (long long)(x >> 40);
-      vb = tile_off[2 * tile + 1] + (long long)(x & ((1ull << 40) - 1));
+      pl = (long long)(x >> 40);
+      vl = (long long)(x & ((1ull << 40) - 1));
+      tc = (long long)(t0 >> 40);
+      tl = (long long)(t0 & ((1ull << 40) - 1));
     } else {
-      long long t0, t1;
-      pb = tile_off[2 * tile] + block_exclusive_scan(c, &t0, sh);
-      vb = tile_off[2 * tile + 1] + block_exclusive_scan(l, &t1, sh);
+      pl = block_exclusive_scan(c, &tc, sh);
+      vl = block_exclusive_scan(l, &tl, sh);
+    }
+    long long pb, vb;
+    {
+      if (threadIdx.x < 32) {
+        const long long ex = lookback_warp(status, tile, (tc << 33) | tl, C);
+        if (threadIdx.x == 0) {
+          s_p = ex >> 33;
+          s_v = ex & ((1ll << 33) - 1);
+          if (tile == ntiles - 1) {
+            const long long np = s_p + tc, nv = s_v + tl;
+            C->n_poly = np;
+            C->n_vtx = nv;
+            if (np <= m) off[np] = nv;
+            else set_error(C, POLYLLA_ERR_LIMIT, 82);
+          }
+        }
+      }
+      __syncthreads();
+      pb = s_p + pl;
+      vb = s_v + vl;
     }
     bool ok = i < n;
     if (ok && (pb + c > m || vb + l > 3 * m)) {
@@ -122,9 +131,9 @@ __global__ void __launch_bounds__(kBlock) k_final_write(PolyArrays P, FinalPiece
 }
 
 cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                               const long long* tile_off, long long* off, int* vtx, long long m,
+                               unsigned long long* status, long long* off, int* vtx, long long m,
                                Counters* C, int grid, cudaStream_t s) {
-  k_final_write<<<grid, kBlock, 0, s>>>(P, F, pool, tile_off, off, vtx, m, C);
+  k_final_write<<<grid, kBlock, 0, s>>>(P, F, pool, status, off, vtx, m, C);
   return cudaGetLastError();
 }
 

@@ -293,8 +293,18 @@ cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* 
 }
 
 // ------------------------------------------------------------------ tile scan
-// One block: exclusive scan of the per-tile pairs (thread i owns a contiguous
-// run of tiles), with the totals and the optional CSR end marker.
+// Exclusive scan of the per-tile pairs by up to kScanBlocks blocks, none waiting
+// for another: block b owns a contiguous range of tiles, first sums every tile
+// before its range (coalesced, the carry), then scans its range (thread i a
+// contiguous run of it).  The last block writes the totals and the optional CSR
+// end marker.  Reads: at most kScanBlocks / 2 times the tile array.
+constexpr int kScanBlocks = 64;
+
+__device__ __forceinline__ int scan_blocks_for(long long ntiles) {
+  const long long b = (ntiles + kScanThreads - 1) / kScanThreads;
+  return (int)(b < 1 ? 1 : (b > kScanBlocks ? kScanBlocks : b));
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(
     const long long* __restrict__ tile_sum, long long* __restrict__ tile_off, long long n_host,
     const long long* n_dev, int tile, long long* tot0, long long* tot1, long long* end,
@@ -302,16 +312,49 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(
   __shared__ long long sh0[32], sh1[32];
   const long long n = n_dev ? *n_dev : n_host;
   const long long ntiles = (n + tile - 1) / tile;
-  const long long per = (ntiles + kScanThreads - 1) / kScanThreads;
-  const long long lo = threadIdx.x * per;
-  const long long hi = min(lo + per, ntiles);
-  long long s0 = 0, s1 = 0;
-  for (long long i = lo; i < hi; ++i) {
-    s0 += tile_sum[2 * i];
-    s1 += tile_sum[2 * i + 1];
-  }
-  // block scan of (s0, s1) over 1024 threads
+  const int nb = scan_blocks_for(ntiles);
+  if ((int)blockIdx.x >= nb) return;
+  const long long per_block = (ntiles + nb - 1) / nb;
+  const long long b0 = (long long)blockIdx.x * per_block;
+  const long long b1 = min(b0 + per_block, ntiles);
+  const longlong2* ts = reinterpret_cast<const longlong2*>(tile_sum);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // carry: every tile before this block's range
+  long long c0 = 0, c1 = 0;
+#pragma unroll 4
+  for (long long i = threadIdx.x; i < b0; i += kScanThreads) {
+    const longlong2 v = ts[i];
+    c0 += v.x;
+    c1 += v.y;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    c0 += __shfl_xor_sync(0xffffffffu, c0, d);
+    c1 += __shfl_xor_sync(0xffffffffu, c1, d);
+  }
+  if (lane == 0) {
+    sh0[warp] = c0;
+    sh1[warp] = c1;
+  }
+  __syncthreads();
+  c0 = 0;
+  c1 = 0;
+  for (int w = 0; w < kScanThreads / 32; ++w) {
+    c0 += sh0[w];
+    c1 += sh1[w];
+  }
+  __syncthreads();
+  // this block's range: thread i owns a contiguous run
+  const long long per = (b1 - b0 + kScanThreads - 1) / kScanThreads;
+  const long long lo = min(b0 + threadIdx.x * per, b1);
+  const long long hi = min(lo + per, b1);
+  long long s0 = 0, s1 = 0;
+#pragma unroll 8
+  for (long long i = lo; i < hi; ++i) {
+    const longlong2 v = ts[i];
+    s0 += v.x;
+    s1 += v.y;
+  }
   long long x0 = s0, x1 = s1;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -340,16 +383,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(
     sh1[lane] = w1;
   }
   __syncthreads();
-  long long p0 = (warp ? sh0[warp - 1] : 0) + x0 - s0;
-  long long p1 = (warp ? sh1[warp - 1] : 0) + x1 - s1;
+  long long p0 = c0 + (warp ? sh0[warp - 1] : 0) + x0 - s0;
+  long long p1 = c1 + (warp ? sh1[warp - 1] : 0) + x1 - s1;
+  longlong2* to = reinterpret_cast<longlong2*>(tile_off);
+#pragma unroll 8
   for (long long i = lo; i < hi; ++i) {
-    tile_off[2 * i] = p0;
-    tile_off[2 * i + 1] = p1;
-    p0 += tile_sum[2 * i];
-    p1 += tile_sum[2 * i + 1];
+    const longlong2 v = ts[i];
+    to[i] = make_longlong2(p0, p1);
+    p0 += v.x;
+    p1 += v.y;
   }
-  if (threadIdx.x == kScanThreads - 1) {
-    const long long t0 = sh0[31], t1 = sh1[31];
+  if ((int)blockIdx.x == nb - 1 && threadIdx.x == kScanThreads - 1) {
+    const long long t0 = c0 + sh0[31], t1 = c1 + sh1[31];
     if (tot0) *tot0 = t0;
     if (tot1) *tot1 = t1;
     const long long at = (end_mode == 1) ? n : t0;
@@ -365,11 +410,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(
 }
 
 cudaError_t launch_scan_tiles(const long long* tile_sum, long long* tile_off, long long n_host,
-                              const long long* n_dev, int tile, long long* tot0, long long* tot1,
-                              long long* end, int end_mode, long long end_cap, Counters* C,
-                              cudaStream_t s) {
-  k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_sum, tile_off, n_host, n_dev, tile, tot0, tot1, end,
-                                          end_mode, end_cap, C);
+                              const long long* n_dev, long long n_bound, int tile,
+                              long long* tot0, long long* tot1, long long* end, int end_mode,
+                              long long end_cap, Counters* C, cudaStream_t s) {
+  const long long tiles = (n_bound + tile - 1) / tile;
+  long long b = (tiles + kScanThreads - 1) / kScanThreads;
+  if (b < 1) b = 1;
+  if (b > kScanBlocks) b = kScanBlocks;
+  k_scan_tiles<<<(int)b, kScanThreads, 0, s>>>(tile_sum, tile_off, n_host, n_dev, tile, tot0, tot1,
+                                               end, end_mode, end_cap, C);
   return cudaGetLastError();
 }
 

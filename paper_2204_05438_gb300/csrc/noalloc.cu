@@ -110,7 +110,7 @@ extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64
   if (e == cudaSuccess) e = launch_label_max(M, d_lab, C, grid_of(sms, (n_tri + 3) / 4, kBlock), s);
   if (e == cudaSuccess) e = launch_label_class(M, d_lab, tile_sum, nullptr, C, grid_of(sms, n_tri, kTriTile), s);
   if (e == cudaSuccess)
-    e = launch_scan_tiles(tile_sum, tile_off, n_tri, nullptr, kTriTile,
+    e = launch_scan_tiles(tile_sum, tile_off, n_tri, nullptr, n_tri, kTriTile,
                           reinterpret_cast<long long*>(d_n_seeds), &C->scratch0, nullptr, 0, 0, C,
                           s);
   if (e == cudaSuccess)

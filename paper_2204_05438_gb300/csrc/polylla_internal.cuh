@@ -18,6 +18,10 @@ namespace polylla {
 constexpr int kBlock = 256;                    // threads per block, every kernel
 constexpr int kTriPerThread = 4;               // label kernels: 4 triangles = 3 x int4
 constexpr int kTriTile = kBlock * kTriPerThread;  // 1024 triangles per seed-count tile
+// Mesh size limits: half-edge ids fit int32, and the output scan packs a tile
+// prefix's polygon count (< 2^29) and vertex count (< 3m + 2n < 2^33) in one word.
+constexpr long long kMaxTriangles = 1ll << 29;
+constexpr long long kMaxVertices = 1ll << 30;
 constexpr int kWalkThreads = 256;  // k_walk block
 constexpr int kWalkCap = 64;       // longer polygons go to one thread block each (long.cu)
 constexpr int kPolyTile = kBlock;              // per-polygon scans: one polygon per thread
@@ -37,6 +41,7 @@ struct Counters {
   long long n_long;       // polygons longer than the walk cap
   long long n_defer;      // polygons with one tip, left to k_repair_one
   long long n_multi;      // polygons with several tips, left to k_repair_multi
+  long long ticket;       // tile tickets of the single-pass (look-back) scans
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
   int error;              // first device error (polylla_status), 0 if none
@@ -102,6 +107,53 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* sh) {
   return before + x - v;
 }
 
+// ------------------------------------------------------------ look-back scan
+// Single-pass prefix sums over tiles (decoupled look-back): tiles are taken in
+// ticket order, so every predecessor of a tile is already running; each tile
+// publishes its aggregate, then sums its predecessors' words back to the nearest
+// inclusive prefix, then publishes its own.  A status word holds the flag in bits
+// 62-63 (0: not yet, 1: aggregate, 2: inclusive prefix) and the value in bits
+// 0-61, so one 64-bit store publishes both.  The array starts zeroed.
+constexpr unsigned long long kLbAgg = 1ull << 62;
+constexpr unsigned long long kLbPre = 2ull << 62;
+constexpr unsigned long long kLbVal = (1ull << 62) - 1;
+constexpr long long kLbSpin = 1ll << 20;  // polls of one word before giving up
+
+// Warp 0 of the block owning `tile` (aggregate `agg`, the same on every lane):
+// returns the exclusive prefix on every lane and publishes the inclusive one.  A
+// predecessor that never publishes (it cannot, while the tickets are honoured)
+// ends the wait after kLbSpin polls with an error.
+__device__ __forceinline__ long long lookback_warp(unsigned long long* status, long long tile,
+                                                   long long agg, Counters* C) {
+  const int lane = threadIdx.x & 31;
+  volatile unsigned long long* vs = status;
+  if (lane == 0) vs[tile] = (tile == 0 ? kLbPre : kLbAgg) | (unsigned long long)agg;
+  long long excl = 0;
+  for (long long j = tile - 1; j >= 0; j -= 32) {
+    const long long idx = j - lane;
+    unsigned long long w = kLbPre;  // before the first tile: a prefix of 0
+    if (idx >= 0) {
+      long long spins = 0;
+      do {
+        w = vs[idx];
+      } while ((w >> 62) == 0 && ++spins < kLbSpin);
+      if ((w >> 62) == 0) {
+        set_error(C, POLYLLA_ERR_LIMIT, 90);
+        w = kLbPre;
+      }
+    }
+    const unsigned pm = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+    const int last = pm ? __ffs(pm) - 1 : 31;  // lanes 0..last are summed
+    long long v = (lane <= last) ? (long long)(w & kLbVal) : 0;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    excl += v;
+    if (pm) break;
+  }
+  if (lane == 0 && tile > 0) vs[tile] = kLbPre | (unsigned long long)(excl + agg);
+  return excl;
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
   T tot;
@@ -121,10 +173,11 @@ cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* 
 // Exclusive scan of per-tile pairs.  Tile count = ceil(n / tile) with n = *n_dev if
 // n_dev, else n_host.  Totals go to *tot0, *tot1.  end_mode 1: end[n] = total0;
 // end_mode 2: end[total0] = total1 (index checked against end_cap).
+// n_bound: an upper bound of the element count (n_host, or *n_dev on the device).
 cudaError_t launch_scan_tiles(const long long* tile_sum, long long* tile_off, long long n_host,
-                              const long long* n_dev, int tile, long long* tot0, long long* tot1,
-                              long long* end, int end_mode, long long end_cap, Counters* C,
-                              cudaStream_t s);
+                              const long long* n_dev, long long n_bound, int tile,
+                              long long* tot0, long long* tot1, long long* end, int end_mode,
+                              long long end_cap, Counters* C, cudaStream_t s);
 // Per polygon of the traversal (index = seed order), capacity m.
 struct PolyArrays {
   int* start;     // canonical start half-edge of the traversal polygon
@@ -180,11 +233,10 @@ cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seed
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                         const LongList& Lg, int* loc, int* vstamp, int epoch,
                         int repair, Counters* C, int grid, cudaStream_t s);
-// Output: per-tile (polygon count, vertex count); then offsets and the copy.
-cudaError_t launch_final_tiles(const PolyArrays& P, long long* tile_sum, Counters* C, int grid,
-                               cudaStream_t s);
+// Output: the CSR offsets (a look-back scan over `status`, zeroed, one word per
+// 256-polygon tile) and the copy; also C->n_poly, C->n_vtx and off[n_poly].
 cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                               const long long* tile_off, long long* off, int* vtx, long long m,
+                               unsigned long long* status, long long* off, int* vtx, long long m,
                                Counters* C, int grid, cudaStream_t s);
 
 }  // namespace polylla
