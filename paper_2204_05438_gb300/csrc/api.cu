@@ -242,6 +242,9 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   const int g1 = grid_for(h, (M.m + 3) / 4, kBlock);
   POLY_TRY(launch(h, "label_max", s, [&] { return launch_label_max(M, h->lab, h->C, g1, s); }));
   const int g2 = grid_for(h, M.m, kTriTile);
+  // per-tile seed counts are accumulated by atomics
+  const long long ntiles = (M.m + kTriTile - 1) / kTriTile;
+  POLY_TRY(cuda_status(cudaMemsetAsync(h->tile_sum, 0, 2 * sizeof(long long) * (size_t)ntiles, s)));
   POLY_TRY(launch(h, "label_class", s, [&] {
     return launch_label_class(M, h->lab, h->tile_sum, h->tf, h->C, g2, s);
   }));

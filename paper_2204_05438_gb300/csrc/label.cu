@@ -157,14 +157,16 @@ cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int gr
 //   seed         <=> terminal and (g_k* < 0 or t < triangle(g_k*))
 // Neighbour label bytes are read while other threads rewrite them; only their
 // bits 0-1 (the Max array, written by the previous kernel) are used, and every
-// rewrite keeps those bits.
+// rewrite keeps those bits, so any version of a byte gives the same answer.
 // When tf is given, also writes tf[h] = twin(h) with bit 31 set iff h is frontier
 // (0x7fffffff as the twin of a border half-edge): one load then tells both
 // whether a walk stops at h and where it turns next.
-__global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
-                                                        long long* __restrict__ tile_sum,
-                                                        int* __restrict__ tf, Counters* C) {
-  __shared__ int sh[kBlock / 32];
+// The seed counts are summed per warp and added to the tile's count with one
+// atomic (tile_sum zeroed beforehand), so no barrier holds a block to its slowest
+// warp.
+__global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* lab,
+                                                           long long* __restrict__ tile_sum,
+                                                           int* __restrict__ tf, Counters* C) {
   const long long m = M.m;
   const long long H = 3 * m;
   const long long ntiles = (m + kTriTile - 1) / kTriTile;
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
       const bool full = t0 + 4 <= m;
       unsigned own = 0;
       if (full) {
-        own = *reinterpret_cast<const volatile unsigned*>(lab + t0);
+        own = *reinterpret_cast<const unsigned*>(lab + t0);
       } else {
         for (int j = 0; t0 + j < m; ++j) own |= (unsigned)lab[t0 + j] << (8 * j);
       }
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
               continue;
             }
             const int gt = gk / 3;
-            const int nb = *(reinterpret_cast<const volatile uint8_t*>(lab) + gt) & 3;
+            const int nb = lab[gt] & 3;
             nbm |= (unsigned)(nb == gk - 3 * gt) << k;
           }
           const bool fr = (gk < 0) || (k != kst && !((nbm >> k) & 1u));
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
         out |= byte << (8 * j);
       }
       if (full) {
-        *reinterpret_cast<volatile unsigned*>(lab + t0) = out;
+        *reinterpret_cast<unsigned*>(lab + t0) = out;
         if (tf) {
           int4* q = reinterpret_cast<int4*>(tf) + 3 * g;
           q[0] = make_int4(tfo[0], tfo[1], tfo[2], tfo[3]);
@@ -225,17 +227,15 @@ __global__ void __launch_bounds__(kBlock) k_label_class(DevMesh M, uint8_t* lab,
         }
       } else {
         for (int j = 0; t0 + j < m; ++j) {
-          *(reinterpret_cast<volatile uint8_t*>(lab) + t0 + j) = (uint8_t)(out >> (8 * j));
+          lab[t0 + j] = (uint8_t)(out >> (8 * j));
           if (tf)
             for (int k = 0; k < 3; ++k) tf[3 * (t0 + j) + k] = tfo[3 * j + k];
         }
       }
     }
-    const int tot = block_sum(nseed, sh);
-    if (threadIdx.x == 0) {
-      tile_sum[2 * tile] = tot;
-      tile_sum[2 * tile + 1] = 0;
-    }
+    const int tot = __reduce_add_sync(0xffffffffu, nseed);
+    if ((threadIdx.x & 31) == 0 && tot)
+      atomicAdd(reinterpret_cast<unsigned long long*>(tile_sum + 2 * tile), (unsigned long long)tot);
   }
 }
 
@@ -253,34 +253,63 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
                                                        const long long* __restrict__ tile_off,
                                                        int* __restrict__ seeds,
                                                        int* __restrict__ entry) {
-  __shared__ int sh[kBlock / 32];
-  const long long ntiles = (m + kTriTile - 1) / kTriTile;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long t0 = 4 * (tile * kBlock + threadIdx.x);
-    unsigned own = 0;
-    if (t0 + 4 <= m) {
-      own = __ldg(reinterpret_cast<const unsigned*>(lab + t0));
+  // 16 triangles per thread (one 16-byte label load): a block covers four
+  // 1024-triangle tiles, two warps each
+  constexpr int kPer = 16;
+  constexpr int kTilesPerBlock = kBlock * kPer / kTriTile;
+  __shared__ int sw[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long nbt = (m + (long long)kBlock * kPer - 1) / ((long long)kBlock * kPer);
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(lab) & 15u) == 0;
+  for (long long bt = blockIdx.x; bt < nbt; bt += gridDim.x) {
+    const long long t0 = (bt * kBlock + threadIdx.x) * kPer;
+    unsigned w[4] = {0, 0, 0, 0};
+    if (t0 + kPer <= m && aligned16) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(lab) + (t0 / kPer));
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    } else if (t0 + kPer <= m) {  // a caller's label array aligned to 4 bytes only
+      const unsigned* l4 = reinterpret_cast<const unsigned*>(lab + t0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = __ldg(l4 + q);
     } else {
-      for (int j = 0; t0 + j < m; ++j) own |= (unsigned)__ldg(lab + t0 + j) << (8 * j);
+      for (int j = 0; j < kPer && t0 + j < m; ++j) w[j >> 2] |= (unsigned)__ldg(lab + t0 + j) << (8 * (j & 3));
     }
     int cnt = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) cnt += (own >> (8 * j + 5)) & 1;
-    int tot;
-    int pos = block_exclusive_scan(cnt, &tot, sh);
-    const long long base = tile_off[2 * tile] + pos;
-    int w = 0;
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const unsigned b = own >> (8 * j);
-      if ((b >> 5) & 1) {
-        const int t = (int)(t0 + j);
-        seeds[base + w] = t;
-        if (entry) {
-          const unsigned fr = (b >> 2) & 7u;
-          entry[base + w] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
+      for (int j = 0; j < 4; ++j) cnt += (w[q] >> (8 * j + 5)) & 1;
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    // tile of this warp: (bt * kTilesPerBlock + warp / 2); the second warp of a
+    // tile starts after the first one's total
+    const long long tile = bt * kTilesPerBlock + (warp >> 1);
+    const long long tb = t0 < m ? tile_off[2 * tile] : 0;
+    long long pos = tb + ((warp & 1) ? sw[warp - 1] : 0) + incl - cnt;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const unsigned b = w[q] >> (8 * j);
+        if ((b >> 5) & 1u) {
+          const int t = (int)(t0 + 4 * q + j);
+          seeds[pos] = t;
+          if (entry) {
+            const unsigned fr = (b >> 2) & 7u;
+            entry[pos] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
+          }
+          ++pos;
         }
-        ++w;
       }
     }
   }

@@ -19,7 +19,8 @@
 //   * the scratch array (about 2 MiB) is part of the library image: every GPU that
 //     loads the library holds it until the process exits;
 //   * every call on a device uses the same array and leaves its contents behind;
-//     the parts that must start at zero are cleared at the start of each call, so
+//     the parts that must start at zero (the error word, the counters and the
+//     per-tile seed counts) are cleared at the start of each call, so
 //     consecutive calls are independent, but calls that overlap on the GPU (two
 //     streams, or two host threads at once) race on it and must be serialised by
 //     the caller;
@@ -105,8 +106,10 @@ extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64
   M.twin = d_twin;
   M.n = n_vertices;
   M.m = n_tri;
-  // the error word and counters start at zero; tile sums are fully rewritten
+  // the error word, counters and tile sums start at zero
   cudaError_t e = cudaMemsetAsync(C, 0, sizeof(Counters), s);
+  const long long ntiles = (n_tri + kTriTile - 1) / kTriTile;  // counts accumulate by atomics
+  if (e == cudaSuccess) e = cudaMemsetAsync(tile_sum, 0, 2 * sizeof(long long) * (size_t)ntiles, s);
   if (e == cudaSuccess) e = launch_label_max(M, d_lab, C, grid_of(sms, (n_tri + 3) / 4, kBlock), s);
   if (e == cudaSuccess) e = launch_label_class(M, d_lab, tile_sum, nullptr, C, grid_of(sms, n_tri, kTriTile), s);
   if (e == cudaSuccess)
