@@ -89,7 +89,7 @@ __device__ __forceinline__ long long sqdist(longlong2 p, longlong2 q) {
 // ------------------------------------------------------------------ LabelMax
 // Longest edge by (exact squared length, then lower undirected id min(h, twin(h))).
 // The twin array is read only for triangles whose longest length is tied.
-__global__ void __launch_bounds__(kBlock) k_label_max(DevMesh M, uint8_t* __restrict__ lab,
+__global__ void __launch_bounds__(kBlock, 6) k_label_max(DevMesh M, uint8_t* __restrict__ lab,
                                                       Counters* C) {
   const long long m = M.m, n = M.n;
   const long long ngroups = (m + 3) / 4;
@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(kBlock) k_label_max(DevMesh M, uint8_t* __rest
 
 cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int grid,
                              cudaStream_t s) {
+  static int cap = 0;
+  grid = resident_grid(reinterpret_cast<const void*>(k_label_max), kBlock, 0, grid, &cap);
   k_label_max<<<grid, kBlock, 0, s>>>(M, lab, C);
   return cudaGetLastError();
 }
@@ -241,6 +243,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* l
 
 cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, int* tf,
                                Counters* C, int grid, cudaStream_t s) {
+  static int cap = 0;
+  grid = resident_grid(reinterpret_cast<const void*>(k_label_class), kBlock, 0, grid, &cap);
   k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tile_sum, tf, C);
   return cudaGetLastError();
 }
@@ -254,15 +258,19 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
                                                        int* __restrict__ seeds,
                                                        int* __restrict__ entry) {
   // 16 triangles per thread (one 16-byte label load): a block covers four
-  // 1024-triangle tiles, two warps each
+  // consecutive 1024-triangle tiles, whose seeds are one contiguous run of the
+  // output; they are staged in shared memory and written out coalesced
   constexpr int kPer = 16;
   constexpr int kTilesPerBlock = kBlock * kPer / kTriTile;
+  constexpr int kSpan = kBlock * kPer;
   __shared__ int sw[kBlock / 32];
+  __shared__ int s_seed[kSpan], s_entry[kSpan];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long nbt = (m + (long long)kBlock * kPer - 1) / ((long long)kBlock * kPer);
+  const long long nbt = (m + kSpan - 1) / kSpan;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(lab) & 15u) == 0;
   for (long long bt = blockIdx.x; bt < nbt; bt += gridDim.x) {
     const long long t0 = (bt * kBlock + threadIdx.x) * kPer;
+    const long long base = tile_off[2 * (bt * kTilesPerBlock)];
     unsigned w[4] = {0, 0, 0, 0};
     if (t0 + kPer <= m && aligned16) {
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(lab) + (t0 / kPer));
@@ -290,12 +298,13 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
     }
     if (lane == 31) sw[warp] = incl;
     __syncthreads();
-    // tile of this warp: (bt * kTilesPerBlock + warp / 2); the second warp of a
-    // tile starts after the first one's total
-    const long long tile = bt * kTilesPerBlock + (warp >> 1);
-    const long long tb = t0 < m ? tile_off[2 * tile] : 0;
-    long long pos = tb + ((warp & 1) ? sw[warp - 1] : 0) + incl - cnt;
-    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int v = 0; v < kBlock / 32; ++v) {
+      before += (v < warp) ? sw[v] : 0;
+      total += sw[v];
+    }
+    int pos = before + incl - cnt;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
 #pragma unroll
@@ -303,20 +312,26 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
         const unsigned b = w[q] >> (8 * j);
         if ((b >> 5) & 1u) {
           const int t = (int)(t0 + 4 * q + j);
-          seeds[pos] = t;
-          if (entry) {
-            const unsigned fr = (b >> 2) & 7u;
-            entry[pos] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
-          }
+          const unsigned fr = (b >> 2) & 7u;
+          s_seed[pos] = t;
+          s_entry[pos] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
           ++pos;
         }
       }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < total; k += kBlock) {
+      seeds[base + k] = s_seed[k];
+      if (entry) entry[base + k] = s_entry[k];
+    }
+    __syncthreads();
   }
 }
 
 cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
                               int* seeds, int* entry, int grid, cudaStream_t s) {
+  static int cap = 0;
+  grid = resident_grid(reinterpret_cast<const void*>(k_seed_write), kBlock, 0, grid, &cap);
   k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, tile_off, seeds, entry);
   return cudaGetLastError();
 }

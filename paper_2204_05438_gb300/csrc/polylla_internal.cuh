@@ -161,6 +161,29 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return tot;
 }
 
+// ----------------------------------------------------------------- grid sizing
+// Grid-stride kernels launch at most one full wave: the blocks that fit on all
+// SMs at once (from the occupancy calculator, cached per kernel in *cache),
+// and no more than `want` blocks.  A second, partial wave would leave its blocks
+// with as many iterations as the first wave's, after it.
+inline int resident_grid(const void* kernel, int threads, size_t smem, long long want,
+                         int* cache) {
+  if (*cache <= 0) {
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+      sms = 1;
+    *cache = per_sm * sms;
+  }
+  long long g = want < *cache ? want : *cache;
+  return (int)(g < 1 ? 1 : g);
+}
+
 // ----------------------------------------------------------------- launchers
 // Every launcher enqueues one kernel on `s` and returns the launch error.
 cudaError_t launch_validate(const DevMesh& M, Counters* C, int grid, cudaStream_t s);

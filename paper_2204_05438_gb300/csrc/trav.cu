@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const int* __restric
 
 cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
                         cudaStream_t s) {
+  static int cap = 0;
+  grid = resident_grid(reinterpret_cast<const void*>(k_succ), kBlock, 0, grid, &cap);
   k_succ<<<grid, kBlock, 0, s>>>(M, tf, succ, C);
   return cudaGetLastError();
 }
@@ -224,6 +226,8 @@ cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* 
     cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
+  static int cap = 0;
+  grid = resident_grid(reinterpret_cast<const void*>(k_walk), kWalkThreads, smem, grid, &cap);
   k_walk<<<grid, kWalkThreads, smem, s>>>(M, tf, entry, succ, P, pool, Lg, D1, Dm, repair, C);
   return cudaGetLastError();
 }
@@ -556,7 +560,10 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                               const LongList& D1, Counters* C, int sms, cudaStream_t s) {
-  k_repair_one<<<sms * 8, kBlock, 0, s>>>(M, lab, tf, succ, P, F, pool, D1, C);
+  static int cap = 0;
+  const int grid = resident_grid(reinterpret_cast<const void*>(k_repair_one), kBlock, 0,
+                                 (long long)sms * 8, &cap);
+  k_repair_one<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, P, F, pool, D1, C);
   return cudaGetLastError();
 }
 
