@@ -219,6 +219,69 @@ polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64_t n_vertic
                                            int64_t n_tri, uint8_t* d_lab, int32_t* d_seeds,
                                            int64_t* d_n_seeds, void* stream);
 
+/*
+ * Batches: many independent meshes in one run (the paper meshes one
+ * triangulation at a time; this form has no counterpart there).
+ *
+ * The meshes are given concatenated, with mesh-local ids:
+ *   d_xy      int64[2 * vtx_off[n]]: mesh j's vertices are rows vtx_off[j] ..
+ *             vtx_off[j+1]-1 (16-byte aligned; borrowed until destroy);
+ *   d_tri     int32[3 * tri_off[n]]: mesh j's triangles are tri_off[j] ..
+ *             tri_off[j+1]-1, their vertex ids local to mesh j (0-based);
+ *   d_twin    int32[3 * tri_off[n]]: twins as half-edge ids local to mesh j, or -1;
+ *   d_vtx_off, d_tri_off  device int64[n_meshes + 1], starting at 0, each mesh
+ *             with >= 3 vertices and >= 1 triangle; totals as for one mesh
+ *             (< 2^30 vertices, < 2^29 triangles).
+ * polylla_batch_create copies the offsets to the host (synchronises), rewrites
+ * the ids into one disjoint union mesh on the device (handle-owned; local ids
+ * out of range give POLYLLA_ERR_RANGE) and, with POLYLLA_VALIDATE, checks it as
+ * polylla_mesh_create does.
+ *
+ * polylla_batch_run runs the whole path (label, seeds, traversal, reparation) on
+ * every mesh at once: the union is meshed exactly as one mesh would be, so each
+ * mesh's polygons are exactly those it gives alone.  The launches of a schedule
+ * are captured into a CUDA graph on its first use (that call runs eagerly) and
+ * replayed afterwards.  schedule: 0 .. polylla_batch_schedules()-1, or
+ * POLYLLA_SCHEDULE_TUNED for the one polylla_batch_tune picked (tuning first if
+ * needed).  A schedule sets the longest polygon walked by one thread (longer
+ * ones go to one thread block each) and that block's size;
+ * polylla_batch_schedule_info reports both.
+ *
+ * polylla_batch_tune times every schedule on this batch (`reps` graph replays
+ * each, after one warm-up), stores the fastest, and returns it in *best and the
+ * mean milliseconds per run in ms[k] (either may be NULL).  Synchronises.
+ *
+ * polylla_batch_get (synchronises): mesh j's polygons.  *d_off points at
+ * n_poly + 1 offsets into *d_vtx (the whole batch's vertex array); polygon k's
+ * vertices are (*d_vtx)[(*d_off)[k] .. (*d_off)[k+1]).  Vertex ids index the
+ * concatenated d_xy (subtract vtx_off[j] for mesh-local ids).  n_vtx is the
+ * mesh's vertex-slot count.  polylla_batch_get_all returns the whole CSR and
+ * d_mesh_first (n_meshes + 1 polygon indices: mesh j owns polygons
+ * d_mesh_first[j] .. d_mesh_first[j+1]-1).  The pointers stay valid until the
+ * next run or destroy.  polylla_batch_mesh returns the union's handle (for
+ * statistics and timing; do not destroy it).
+ */
+typedef struct polylla_batch* polylla_batch_t;
+#define POLYLLA_SCHEDULE_TUNED (-1)
+
+polylla_status polylla_batch_create(const int64_t* d_xy, const int64_t* d_vtx_off,
+                                    const int32_t* d_tri, const int32_t* d_twin,
+                                    const int64_t* d_tri_off, int64_t n_meshes, uint32_t flags,
+                                    void* stream, polylla_batch_t* out);
+int polylla_batch_schedules(void);
+polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_threads);
+polylla_status polylla_batch_tune(polylla_batch_t batch, int reps, void* stream, int* best,
+                                  float* ms);
+polylla_status polylla_batch_run(polylla_batch_t batch, int schedule, void* stream);
+polylla_status polylla_batch_get(polylla_batch_t batch, int64_t mesh, const int64_t** d_off,
+                                 const int32_t** d_vtx, int64_t* n_poly, int64_t* n_vtx);
+polylla_status polylla_batch_get_all(polylla_batch_t batch, const int64_t** d_off,
+                                     const int32_t** d_vtx, const int64_t** d_mesh_first,
+                                     int64_t* n_poly, int64_t* n_vtx);
+polylla_status polylla_batch_stats(polylla_batch_t batch, polylla_stats* out);
+polylla_mesh_t polylla_batch_mesh(polylla_batch_t batch);
+polylla_status polylla_batch_destroy(polylla_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

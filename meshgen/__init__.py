@@ -192,6 +192,35 @@ def batch(ns, seeds, kinds, sides, threads: int | None = None) -> list[dict]:
     return out
 
 
+def batch_plan(count: int, seed: int, nmin: int = 200, nmax: int = 200_000,
+               side: int = 1 << 22) -> dict:
+    """Sizes, seeds and kinds of a batch of meshes: point counts log-uniform in
+    [nmin, nmax], uniform or 16-component Gaussian mixture per mesh, all drawn from
+    one seeded generator (numpy's PCG64 -- a driver of the workload, not of the
+    method)."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(nmin), np.log(nmax), count)).astype(np.int64)
+    ns = np.maximum(ns, 3)
+    return {"ns": ns, "seeds": rng.integers(1, 2**63 - 1, count, dtype=np.int64).astype(np.uint64),
+            "kinds": rng.integers(0, 2, count).astype(np.int32),
+            "sides": np.full(count, side, dtype=np.int64)}
+
+
+def concat(meshes: list) -> dict:
+    """Concatenate meshes for a batch: xy / tri / twin stacked with ids kept local to
+    each mesh, and the vertex and triangle offsets (int64, n + 1 entries)."""
+    nv = np.array([m["xy"].shape[0] for m in meshes], dtype=np.int64)
+    nt = np.array([m["tri"].shape[0] for m in meshes], dtype=np.int64)
+    vtx_off = np.zeros(len(meshes) + 1, dtype=np.int64)
+    tri_off = np.zeros(len(meshes) + 1, dtype=np.int64)
+    vtx_off[1:] = np.cumsum(nv)
+    tri_off[1:] = np.cumsum(nt)
+    return {"xy": np.ascontiguousarray(np.concatenate([m["xy"] for m in meshes])),
+            "tri": np.ascontiguousarray(np.concatenate([m["tri"] for m in meshes])),
+            "twin": np.ascontiguousarray(np.concatenate([m["twin"] for m in meshes])),
+            "vtx_off": vtx_off, "tri_off": tri_off}
+
+
 def twin_from_tri(tri) -> np.ndarray:
     """Half-edge twin array of a triangle list (for hand-built meshes).
 

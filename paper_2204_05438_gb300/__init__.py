@@ -89,6 +89,20 @@ def load_library(path: str | None = None):
                                       ctypes.POINTER(ctypes.c_float), i64, i32], i64),
             "polylla_launch_count": ([vp], i64),
             "polylla_label_seeds_noalloc": ([vp, i64, vp, vp, i64, vp, vp, vp, vp], st),
+            "polylla_batch_create": ([vp, vp, vp, vp, vp, i64, u32, vp, ctypes.POINTER(vp)], st),
+            "polylla_batch_schedules": ([], i32),
+            "polylla_batch_schedule_info": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+            "polylla_batch_tune": ([vp, i32, vp, ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_float)], st),
+            "polylla_batch_run": ([vp, i32, vp], st),
+            "polylla_batch_get": ([vp, i64, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   ctypes.POINTER(i64), ctypes.POINTER(i64)], st),
+            "polylla_batch_get_all": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                       ctypes.POINTER(i64)], st),
+            "polylla_batch_stats": ([vp, ctypes.POINTER(Stats)], st),
+            "polylla_batch_mesh": ([vp], vp),
+            "polylla_batch_destroy": ([vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -261,6 +275,91 @@ def label_seeds_noalloc(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
         _stream(stream)), "polylla_label_seeds_noalloc")
 
 
+SCHEDULE_TUNED = -1
+
+
+def batch_create(xy: torch.Tensor, vtx_off: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
+                 tri_off: torch.Tensor, flags: int = VALIDATE, stream=None) -> int:
+    """Concatenated meshes with local ids (see polylla_batch_create)."""
+    out = ctypes.c_void_p()
+    n = vtx_off.numel() - 1
+    if tri_off.numel() - 1 != n:
+        raise ValueError("vtx_off and tri_off must describe the same number of meshes")
+    _check(load_library().polylla_batch_create(
+        _dptr(xy, torch.int64, "xy"), _dptr(vtx_off, torch.int64, "vtx_off"),
+        _dptr(tri, torch.int32, "tri"), _dptr(twin, torch.int32, "twin"),
+        _dptr(tri_off, torch.int64, "tri_off"), n, flags, _stream(stream), ctypes.byref(out)),
+        "polylla_batch_create")
+    return out.value
+
+
+def batch_schedules() -> int:
+    return int(load_library().polylla_batch_schedules())
+
+
+def batch_schedule_info(schedule: int) -> dict:
+    cap, thr = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().polylla_batch_schedule_info(schedule, ctypes.byref(cap),
+                                                      ctypes.byref(thr)),
+           "polylla_batch_schedule_info")
+    return {"walk_cap": cap.value, "long_threads": thr.value}
+
+
+def batch_tune(batch: int, reps: int = 3, stream=None):
+    """Time every schedule; returns (best, [ms per run for each schedule])."""
+    k = batch_schedules()
+    best = ctypes.c_int()
+    ms = (ctypes.c_float * k)()
+    _check(load_library().polylla_batch_tune(batch, reps, _stream(stream), ctypes.byref(best), ms),
+           "polylla_batch_tune")
+    return best.value, [float(x) for x in ms]
+
+
+def batch_run(batch: int, schedule: int = SCHEDULE_TUNED, stream=None):
+    _check(load_library().polylla_batch_run(batch, schedule, _stream(stream)), "polylla_batch_run")
+
+
+def batch_get(batch: int, mesh: int):
+    """Mesh `mesh`'s polygons: (off int64 [np+1], vtx int32 view of the whole batch);
+    polygon k is vtx[off[k]:off[k+1]], ids into the concatenated xy."""
+    po, pv = ctypes.c_void_p(), ctypes.c_void_p()
+    npoly, nv = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().polylla_batch_get(batch, mesh, ctypes.byref(po), ctypes.byref(pv),
+                                            ctypes.byref(npoly), ctypes.byref(nv)),
+           "polylla_batch_get")
+    off = torch.as_tensor(_DeviceArray(po.value, npoly.value + 1, "<i8"), device="cuda")
+    end = int(off[-1].item()) if npoly.value >= 0 else 0
+    return off, _view(pv.value, end, "<i4", torch.int32)
+
+
+def batch_get_all(batch: int, n_meshes: int):
+    """(off int64 [np+1], vtx int32 [nv], mesh_first int64 [n_meshes+1]) of the whole
+    batch: mesh j owns polygons mesh_first[j] .. mesh_first[j+1]-1."""
+    po, pv, pf = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    npoly, nv = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().polylla_batch_get_all(batch, ctypes.byref(po), ctypes.byref(pv),
+                                                ctypes.byref(pf), ctypes.byref(npoly),
+                                                ctypes.byref(nv)),
+           "polylla_batch_get_all")
+    off = torch.as_tensor(_DeviceArray(po.value, npoly.value + 1, "<i8"), device="cuda")
+    first = torch.as_tensor(_DeviceArray(pf.value, n_meshes + 1, "<i8"), device="cuda")
+    return off, _view(pv.value, nv.value, "<i4", torch.int32), first
+
+
+def batch_stats(batch: int) -> dict:
+    s = Stats()
+    _check(load_library().polylla_batch_stats(batch, ctypes.byref(s)), "polylla_batch_stats")
+    return s.as_dict()
+
+
+def batch_mesh(batch: int) -> int:
+    return load_library().polylla_batch_mesh(batch)
+
+
+def batch_destroy(batch: int):
+    _check(load_library().polylla_batch_destroy(batch), "polylla_batch_destroy")
+
+
 # ------------------------------------------------------------------ convenience
 class Mesh:
     """Owns a handle over device tensors (kept alive here) and runs the phases."""
@@ -308,6 +407,53 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Owns a batch handle over concatenated device tensors (kept alive here)."""
+
+    def __init__(self, xy: torch.Tensor, vtx_off: torch.Tensor, tri: torch.Tensor,
+                 twin: torch.Tensor, tri_off: torch.Tensor, validate: bool = True, stream=None):
+        self.xy, self.vtx_off, self.tri, self.twin, self.tri_off = xy, vtx_off, tri, twin, tri_off
+        self.n_meshes = vtx_off.numel() - 1
+        self.handle = batch_create(xy, vtx_off, tri, twin, tri_off,
+                                   VALIDATE if validate else 0, stream)
+
+    def tune(self, reps: int = 3, stream=None):
+        return batch_tune(self.handle, reps, stream)
+
+    def run(self, schedule: int = SCHEDULE_TUNED, stream=None):
+        batch_run(self.handle, schedule, stream)
+
+    def polygons(self, mesh: int):
+        return batch_get(self.handle, mesh)
+
+    def all_polygons(self):
+        return batch_get_all(self.handle, self.n_meshes)
+
+    def stats(self) -> dict:
+        return batch_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_from_numpy(cat: dict, device: str = "cuda", validate: bool = True, stream=None) -> Batch:
+    """Upload concatenated meshes (xy, vtx_off, tri, tri_off, twin numpy arrays, ids local
+    to each mesh) and create a batch handle."""
+    def dev(a, dt):
+        return torch.as_tensor(a).to(device=device, dtype=dt).contiguous()
+    return Batch(dev(cat["xy"], torch.int64), dev(cat["vtx_off"], torch.int64),
+                 dev(cat["tri"], torch.int32), dev(cat["twin"], torch.int32),
+                 dev(cat["tri_off"], torch.int64), validate=validate, stream=stream)
 
 
 def from_numpy(mesh: dict, device: str = "cuda", validate: bool = True, stream=None) -> Mesh:

@@ -64,6 +64,11 @@ struct polylla_mesh {
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 
+  // schedule: the walk's thread-per-seed cap and the long-polygon block size
+  int walk_cap = kWalkCap;
+  int long_threads = 512;
+  long long* obase = nullptr;  // batches: output index of each traversal polygon
+
   bool timing = false;
   std::vector<TimingRec> recs;
   std::vector<cudaEvent_t> event_pool;
@@ -281,8 +286,8 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   }
   const int gw = grid_for(h, M.m, 4 * 256);
   POLY_TRY(launch(h, "walk", s, [&] {
-    return launch_walk(M, h->tf, h->entry, h->succ, h->P, h->pool, h->Lg, h->Dl, h->Dm, repair,
-                       h->C, gw, s);
+    return launch_walk(M, h->tf, h->entry, h->succ, h->P, h->pool, h->Lg, h->Dl, h->Dm,
+                       h->walk_cap, repair, h->C, gw, s);
   }));
   // repair_one (this stream), repair_multi and long (side streams) at once
   const bool fork = !h->timing;
@@ -296,7 +301,8 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   }
   POLY_TRY(launch(h, "long", s1, [&] {
     return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg,
-                       h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->C, 2 * h->sms, s1);
+                       h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->long_threads, h->C,
+                       2 * h->sms, s1);
   }));
   if (repair) {
     POLY_TRY(launch(h, "repair_multi", s2, [&] {
@@ -322,7 +328,7 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   POLY_TRY(cuda_status(
       cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)ntiles, s)));
   return launch(h, "out_write", s, [&] {
-    return launch_final_write(h->P, h->F, h->pool, status, off, vtx, M.m, h->C, gt, s);
+    return launch_final_write(h->P, h->F, h->pool, status, off, vtx, h->obase, M.m, h->C, gt, s);
   });
 }
 
@@ -352,6 +358,116 @@ polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags) {
     polylla_status st = read_counters(h, &c);
     if (st != POLYLLA_OK) return st;
   }
+  return POLYLLA_OK;
+}
+
+// ---------------------------------------------------------------- batches
+// Schedules a batch can be run with (walk cap, long-polygon block threads).
+constexpr int kSchedules = 4;
+constexpr int kSchedCap[kSchedules] = {64, 32, 48, 64};
+constexpr int kSchedLong[kSchedules] = {512, 512, 512, 256};
+
+}  // namespace
+
+struct polylla_batch {
+  polylla_mesh* mesh = nullptr;  // the union of the meshes
+  int* tri_g = nullptr;          // union ids
+  int* twin_g = nullptr;
+  long long n_meshes = 0;
+  long long* d_tri_off = nullptr;
+  long long* d_vtx_off = nullptr;
+  long long* d_pfirst = nullptr;
+  long long* d_obase = nullptr;
+  std::vector<long long> pfirst;  // host copy, read after a run
+  bool pfirst_valid = false;
+  int tuned = -1;
+  cudaGraphExec_t exec[kSchedules] = {};
+  // graphs are captured and replayed on this stream (the caller's may be the
+  // legacy default stream, which cannot be captured), joined to the caller's
+  cudaStream_t gs = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+};
+
+namespace {
+
+void batch_free(polylla_batch* b) {
+  for (int k = 0; k < kSchedules; ++k)
+    if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+  if (b->gs) cudaStreamDestroy(b->gs);
+  if (b->in) cudaEventDestroy(b->in);
+  if (b->out) cudaEventDestroy(b->out);
+  if (b->mesh) {
+    free_all(b->mesh);
+    delete b->mesh;
+  }
+  void* ptrs[] = {b->tri_g, b->twin_g, b->d_tri_off, b->d_vtx_off, b->d_pfirst, b->d_obase};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// The whole path over the union plus the per-mesh table, enqueued on s.
+polylla_status batch_body(polylla_batch* b, cudaStream_t s) {
+  polylla_mesh* h = b->mesh;
+  h->last_stream = s;
+  POLY_TRY(do_label(h, s));
+  POLY_TRY(do_seeds(h, s));
+  POLY_TRY(do_repair(h, s));
+  return launch(h, "batch_first", s, [&] {
+    return launch_batch_first(h->seeds, b->d_tri_off, b->n_meshes, b->d_obase, b->d_pfirst, h->C,
+                              s);
+  });
+}
+
+// Run schedule k: the first time eagerly (kernel attributes and occupancy caches
+// are set up outside a capture), then captured into a CUDA graph that later runs
+// replay.  With per-kernel timing on, always eagerly.
+polylla_status batch_run_sched(polylla_batch* b, int k, cudaStream_t s) {
+  polylla_mesh* h = b->mesh;
+  h->walk_cap = kSchedCap[k];
+  h->long_threads = kSchedLong[k];
+  b->pfirst_valid = false;
+  if (h->timing) return batch_body(b, s);
+  if (!b->exec[k]) {
+    POLY_TRY(batch_body(b, s));
+    // capture on the batch's own stream (nothing runs during a capture)
+    cudaGraph_t g = nullptr;
+    POLY_TRY(cuda_status(cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal)));
+    polylla_status st = batch_body(b, b->gs);
+    cudaError_t e = cudaStreamEndCapture(b->gs, &g);
+    h->last_stream = s;
+    if (st != POLYLLA_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    POLY_TRY(cuda_status(e));
+    e = cudaGraphInstantiate(&b->exec[k], g, 0);
+    cudaGraphDestroy(g);
+    POLY_TRY(cuda_status(e));
+    return POLYLLA_OK;  // the captured launches did not run; the eager ones did
+  }
+  POLY_TRY(cuda_status(cudaEventRecord(b->in, s)));
+  POLY_TRY(cuda_status(cudaStreamWaitEvent(b->gs, b->in, 0)));
+  POLY_TRY(cuda_status(cudaGraphLaunch(b->exec[k], b->gs)));
+  POLY_TRY(cuda_status(cudaEventRecord(b->out, b->gs)));
+  POLY_TRY(cuda_status(cudaStreamWaitEvent(s, b->out, 0)));
+  h->last_stream = s;
+  h->phase = kRepaired;
+  h->latest_csr = 1;
+  ++h->launches;
+  return POLYLLA_OK;
+}
+
+polylla_status batch_table(polylla_batch* b) {
+  if (b->pfirst_valid) return POLYLLA_OK;
+  polylla_mesh* h = b->mesh;
+  if (h->phase != kRepaired) return POLYLLA_ERR_STATE;
+  Counters c;
+  POLY_TRY(read_counters(h, &c));  // syncs and reports device errors
+  b->pfirst.assign((size_t)b->n_meshes + 1, 0);
+  POLY_TRY(cuda_status(cudaMemcpy(b->pfirst.data(), b->d_pfirst,
+                                  sizeof(long long) * (size_t)(b->n_meshes + 1),
+                                  cudaMemcpyDeviceToHost)));
+  b->pfirst_valid = true;
   return POLYLLA_OK;
 }
 
@@ -599,5 +715,196 @@ int64_t polylla_kernel_times(polylla_mesh_t h, const char** names, float* ms, in
 }
 
 int64_t polylla_launch_count(polylla_mesh_t h) { return h ? h->launches : -1; }
+
+polylla_status polylla_batch_create(const int64_t* d_xy, const int64_t* d_vtx_off,
+                                    const int32_t* d_tri, const int32_t* d_twin,
+                                    const int64_t* d_tri_off, int64_t n_meshes, uint32_t flags,
+                                    void* stream, polylla_batch_t* out) {
+  if (!out) return POLYLLA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d_xy || !d_vtx_off || !d_tri || !d_twin || !d_tri_off || n_meshes < 1)
+    return POLYLLA_ERR_INVALID_ARG;
+  if ((flags & ~POLYLLA_VALIDATE) != 0) return POLYLLA_ERR_INVALID_ARG;
+  if (((uintptr_t)d_xy | (uintptr_t)d_tri | (uintptr_t)d_twin) & 15u) return POLYLLA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<long long> to((size_t)n_meshes + 1), vo((size_t)n_meshes + 1);
+  if (cudaMemcpy(to.data(), d_tri_off, sizeof(long long) * to.size(), cudaMemcpyDeviceToHost) !=
+          cudaSuccess ||
+      cudaMemcpy(vo.data(), d_vtx_off, sizeof(long long) * vo.size(), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return POLYLLA_ERR_CUDA;
+  if (to[0] != 0 || vo[0] != 0) return POLYLLA_ERR_INVALID_ARG;
+  for (int64_t j = 0; j < n_meshes; ++j)
+    if (to[(size_t)j + 1] - to[(size_t)j] < 1 || vo[(size_t)j + 1] - vo[(size_t)j] < 3)
+      return POLYLLA_ERR_INVALID_ARG;
+  const long long m = to[(size_t)n_meshes], n = vo[(size_t)n_meshes];
+  if (m >= kMaxTriangles || n >= kMaxVertices) return POLYLLA_ERR_INVALID_ARG;
+  polylla_batch* b = new (std::nothrow) polylla_batch();
+  if (!b) return POLYLLA_ERR_OOM;
+  b->n_meshes = n_meshes;
+  polylla_mesh* h = new (std::nothrow) polylla_mesh();
+  if (!h) {
+    delete b;
+    return POLYLLA_ERR_OOM;
+  }
+  b->mesh = h;
+  cudaError_t e = dalloc(&b->tri_g, 3 * m);
+  if (e == cudaSuccess) e = dalloc(&b->twin_g, 3 * m);
+  if (e == cudaSuccess) e = dalloc(&b->d_tri_off, n_meshes + 1);
+  if (e == cudaSuccess) e = dalloc(&b->d_vtx_off, n_meshes + 1);
+  if (e == cudaSuccess) e = dalloc(&b->d_pfirst, n_meshes + 1);
+  if (e == cudaSuccess) e = dalloc(&b->d_obase, m);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->out, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_tri_off, to.data(), sizeof(long long) * to.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_vtx_off, vo.data(), sizeof(long long) * vo.size(), cudaMemcpyHostToDevice);
+  polylla_status st = cuda_status(e);
+  if (st == POLYLLA_OK) {
+    h->M.xy = reinterpret_cast<const long long*>(d_xy);
+    h->M.tri = b->tri_g;
+    h->M.twin = b->twin_g;
+    h->M.n = n;
+    h->M.m = m;
+    h->obase = b->d_obase;
+    st = create_common(h, s, 0);
+  }
+  if (st == POLYLLA_OK) {
+    const int g = grid_for(h, m, kBlock);
+    st = launch(h, "batch_globalize", s, [&] {
+      return launch_batch_globalize(d_tri, d_twin, b->d_tri_off, b->d_vtx_off, n_meshes, m,
+                                    b->tri_g, b->twin_g, h->C, g, s);
+    });
+  }
+  if (st == POLYLLA_OK && (flags & POLYLLA_VALIDATE)) {
+    const int g = grid_for(h, (n > 3 * m ? n : 3 * m), kBlock);
+    st = launch(h, "validate", s, [&] { return launch_validate(h->M, h->C, g, s); });
+  }
+  if (st == POLYLLA_OK) {
+    Counters c;
+    st = read_counters(h, &c);  // range errors of the local ids, validation
+  }
+  if (st != POLYLLA_OK) {
+    batch_free(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return POLYLLA_OK;
+}
+
+int polylla_batch_schedules(void) { return kSchedules; }
+
+polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_threads) {
+  if (schedule < 0 || schedule >= kSchedules) return POLYLLA_ERR_INVALID_ARG;
+  if (walk_cap) *walk_cap = kSchedCap[schedule];
+  if (long_threads) *long_threads = kSchedLong[schedule];
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_batch_tune(polylla_batch_t b, int reps, void* stream, int* best,
+                                  float* ms) {
+  if (!b || reps < 1) return POLYLLA_ERR_INVALID_ARG;
+  POLY_TRY(check_handle(b->mesh));
+  if (b->mesh->timing) return POLYLLA_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return POLYLLA_ERR_CUDA;
+  }
+  polylla_status st = POLYLLA_OK;
+  float best_ms = 0.f;
+  int arg = 0;
+  for (int k = 0; k < kSchedules && st == POLYLLA_OK; ++k) {
+    st = batch_run_sched(b, k, s);                         // builds the graph
+    if (st == POLYLLA_OK) st = batch_run_sched(b, k, s);  // one warm replay
+    if (st != POLYLLA_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == POLYLLA_OK; ++r) st = batch_run_sched(b, k, s);
+    cudaEventRecord(e1, s);
+    if (st == POLYLLA_OK) st = cuda_status(cudaEventSynchronize(e1));
+    float t = 0.f;
+    if (st == POLYLLA_OK) st = cuda_status(cudaEventElapsedTime(&t, e0, e1));
+    t /= (float)reps;
+    if (ms) ms[k] = t;
+    if (k == 0 || t < best_ms) {
+      best_ms = t;
+      arg = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != POLYLLA_OK) return st;
+  Counters c;
+  POLY_TRY(read_counters(b->mesh, &c));  // device errors of the timed runs
+  b->tuned = arg;
+  if (best) *best = arg;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_batch_run(polylla_batch_t b, int schedule, void* stream) {
+  if (!b) return POLYLLA_ERR_INVALID_ARG;
+  POLY_TRY(check_handle(b->mesh));
+  if (schedule == POLYLLA_SCHEDULE_TUNED) {
+    if (b->tuned < 0) POLY_TRY(polylla_batch_tune(b, 3, stream, nullptr, nullptr));
+    schedule = b->tuned;
+  }
+  if (schedule < 0 || schedule >= kSchedules) return POLYLLA_ERR_INVALID_ARG;
+  return batch_run_sched(b, schedule, (cudaStream_t)stream);
+}
+
+polylla_status polylla_batch_get(polylla_batch_t b, int64_t mesh, const int64_t** d_off,
+                                 const int32_t** d_vtx, int64_t* n_poly, int64_t* n_vtx) {
+  if (!b || !d_off || !d_vtx || !n_poly || !n_vtx) return POLYLLA_ERR_INVALID_ARG;
+  POLY_TRY(check_handle(b->mesh));
+  if (mesh < 0 || mesh >= b->n_meshes) return POLYLLA_ERR_INVALID_ARG;
+  POLY_TRY(batch_table(b));
+  const long long p0 = b->pfirst[(size_t)mesh], p1 = b->pfirst[(size_t)mesh + 1];
+  long long v[2] = {0, 0};
+  const long long* off = b->mesh->off_final;
+  if (cudaMemcpy(&v[0], off + p0, sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&v[1], off + p1, sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return POLYLLA_ERR_CUDA;
+  *d_off = reinterpret_cast<const int64_t*>(off + p0);
+  *d_vtx = b->mesh->vtx_final;
+  *n_poly = p1 - p0;
+  *n_vtx = v[1] - v[0];
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_batch_get_all(polylla_batch_t b, const int64_t** d_off,
+                                     const int32_t** d_vtx, const int64_t** d_mesh_first,
+                                     int64_t* n_poly, int64_t* n_vtx) {
+  if (!b || !d_off || !d_vtx || !d_mesh_first || !n_poly || !n_vtx) return POLYLLA_ERR_INVALID_ARG;
+  POLY_TRY(check_handle(b->mesh));
+  POLY_TRY(batch_table(b));
+  Counters c;
+  POLY_TRY(read_counters(b->mesh, &c));
+  *d_off = reinterpret_cast<const int64_t*>(b->mesh->off_final);
+  *d_vtx = b->mesh->vtx_final;
+  *d_mesh_first = reinterpret_cast<const int64_t*>(b->d_pfirst);
+  *n_poly = c.n_poly;
+  *n_vtx = c.n_vtx;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_batch_stats(polylla_batch_t b, polylla_stats* out) {
+  if (!b) return POLYLLA_ERR_INVALID_ARG;
+  return polylla_get_stats(b->mesh, out);
+}
+
+polylla_mesh_t polylla_batch_mesh(polylla_batch_t b) { return b ? b->mesh : nullptr; }
+
+polylla_status polylla_batch_destroy(polylla_batch_t b) {
+  if (!b) return POLYLLA_ERR_INVALID_ARG;
+  POLY_TRY(check_handle(b->mesh));
+  cudaDeviceSynchronize();
+  batch_free(b);
+  delete b;
+  return POLYLLA_OK;
+}
 
 }  // extern "C"

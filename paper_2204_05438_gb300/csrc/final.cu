@@ -30,7 +30,8 @@ __device__ __forceinline__ void out_counts(const PolyArrays& P, long long i, lon
 __global__ void __launch_bounds__(kBlock) k_final_write(PolyArrays P, FinalPieces F, Pool pool,
                                                         unsigned long long* status,
                                                         long long* __restrict__ off,
-                                                        int* __restrict__ vtx, long long m,
+                                                        int* __restrict__ vtx,
+                                                        long long* __restrict__ obase, long long m,
                                                         Counters* C) {
   __shared__ long long sh[kBlock / 32];
   __shared__ unsigned long long shu[kBlock / 32];
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(kBlock) k_final_write(PolyArrays P, FinalPiece
     }
     long long src = -1;
     if (ok) {
+      if (obase) obase[i] = pb;
       const int pc = P.pcnt[i];
       if (pc == 0) {
         src = P.pos[i];
@@ -131,11 +133,12 @@ __global__ void __launch_bounds__(kBlock) k_final_write(PolyArrays P, FinalPiece
 }
 
 cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                               unsigned long long* status, long long* off, int* vtx, long long m,
-                               Counters* C, int grid, cudaStream_t s) {
+                               unsigned long long* status, long long* off, int* vtx,
+                               long long* obase, long long m, Counters* C, int grid,
+                               cudaStream_t s) {
   static int cap = 0;
   grid = resident_grid(reinterpret_cast<const void*>(k_final_write), kBlock, 0, grid, &cap);
-  k_final_write<<<grid, kBlock, 0, s>>>(P, F, pool, status, off, vtx, m, C);
+  k_final_write<<<grid, kBlock, 0, s>>>(P, F, pool, status, off, vtx, obase, m, C);
   return cudaGetLastError();
 }
 

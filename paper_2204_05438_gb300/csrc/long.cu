@@ -610,14 +610,15 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
 cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                         const LongList& Lg, int* loc, int* vstamp, int epoch,
-                        int repair, Counters* C, int grid, cudaStream_t s) {
+                        int repair, int threads, Counters* C, int grid, cudaStream_t s) {
+  if (threads < 128 || threads > kLongThreads || threads % 32) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int) * (size_t)kLongSmemInts;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_long<<<grid, kLongThreads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, loc,
+  k_long<<<grid, threads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, loc,
                                           vstamp, epoch, repair, C);
   return cudaGetLastError();
 }

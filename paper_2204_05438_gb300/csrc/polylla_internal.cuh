@@ -240,10 +240,11 @@ struct LongList {
 cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
                         cudaStream_t s);
 // One thread per seed: walk (<= kWalkCap) and, if `repair`, split the polygon.
+// cap: polygons longer than cap (16, 32, 48 or 64) go to the long-polygon blocks.
 cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
                         const PolyArrays& P, const Pool& pool, const LongList& Lg,
-                        const LongList& D1, const LongList& Dm, int repair, Counters* C, int grid,
-                        cudaStream_t s);
+                        const LongList& D1, const LongList& Dm, int cap, int repair,
+                        Counters* C, int grid, cudaStream_t s);
 // One thread per polygon with one tip / with several tips (listed by k_walk).
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
@@ -255,11 +256,21 @@ cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const i
 cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                         const LongList& Lg, int* loc, int* vstamp, int epoch,
-                        int repair, Counters* C, int grid, cudaStream_t s);
+                        int repair, int threads, Counters* C, int grid, cudaStream_t s);
 // Output: the CSR offsets (a look-back scan over `status`, zeroed, one word per
 // 256-polygon tile) and the copy; also C->n_poly, C->n_vtx and off[n_poly].
+// obase (nullable): per traversal polygon, the index of its first output polygon.
 cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                               unsigned long long* status, long long* off, int* vtx, long long m,
-                               Counters* C, int grid, cudaStream_t s);
+                               unsigned long long* status, long long* off, int* vtx,
+                               long long* obase, long long m, Counters* C, int grid,
+                               cudaStream_t s);
+// Batches: union ids from per-mesh local ids, and each mesh's first output polygon.
+cudaError_t launch_batch_globalize(const int* tri, const int* twin, const long long* tri_off,
+                                   const long long* vtx_off, long long n_meshes, long long m,
+                                   int* tri_g, int* twin_g, Counters* C, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_batch_first(const int* seeds, const long long* tri_off, long long n_meshes,
+                               const long long* obase, long long* pfirst, Counters* C,
+                               cudaStream_t s);
 
 }  // namespace polylla

@@ -104,9 +104,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
                                                        const int* __restrict__ entry,
                                                        const int* __restrict__ succ, PolyArrays P,
                                                        Pool pool, LongList Lg, LongList D1,
-                                                       LongList Dm, int repair, Counters* C) {
+                                                       LongList Dm, int cap, int repair,
+                                                       Counters* C) {
   extern __shared__ int sbuf[];
-  int* my = sbuf + threadIdx.x * kWalkCap;
+  int* my = sbuf + threadIdx.x * cap;
   const long long n = C->n_seeds;
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
             break;
           }
           h = g;
-        } while (h != e && len < kWalkCap);
+        } while (h != e && len < cap);
         closed = ok && h == e;
         is_long = ok && !closed;
         if (!ok) set_error(C, POLYLLA_ERR_LIMIT, 52);
@@ -218,17 +219,21 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
 
 cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
                         const PolyArrays& P, const Pool& pool, const LongList& Lg,
-                        const LongList& D1, const LongList& Dm, int repair, Counters* C, int grid,
-                        cudaStream_t s) {
-  const size_t smem = sizeof(int) * (size_t)kWalkThreads * kWalkCap;
+                        const LongList& D1, const LongList& Dm, int cap, int repair,
+                        Counters* C, int grid, cudaStream_t s) {
+  if (cap < 16 || cap > kWalkCap || cap % 16) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(int) * (size_t)kWalkThreads * cap;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(int) * kWalkThreads * kWalkCap));
     attr = true;
   }
-  static int cap = 0;
-  grid = resident_grid(reinterpret_cast<const void*>(k_walk), kWalkThreads, smem, grid, &cap);
-  k_walk<<<grid, kWalkThreads, smem, s>>>(M, tf, entry, succ, P, pool, Lg, D1, Dm, repair, C);
+  static int resident[kWalkCap / 16 + 1] = {};
+  grid = resident_grid(reinterpret_cast<const void*>(k_walk), kWalkThreads, smem, grid,
+                       &resident[cap / 16]);
+  k_walk<<<grid, kWalkThreads, smem, s>>>(M, tf, entry, succ, P, pool, Lg, D1, Dm, cap, repair,
+                                          C);
   return cudaGetLastError();
 }
 

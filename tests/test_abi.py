@@ -69,3 +69,25 @@ def test_compiled_for_sm103a_only():
     flags = pbuild.compile_flags()
     assert "arch=compute_103a,code=sm_103a" in flags
     assert sum("arch=" in f for f in flags) == 1
+
+
+def test_batch_argument_errors_need_no_device():
+    lib = pg.load_library()
+    b = ctypes.c_void_p(123)
+    assert lib.polylla_batch_create(None, None, None, None, None, 1, 0, None, None) == 1
+    assert lib.polylla_batch_create(None, None, None, None, None, 1, 0, None, ctypes.byref(b)) == 1
+    assert b.value is None
+    assert lib.polylla_batch_create(16, 16, 16, 16, 16, 0, 0, None, ctypes.byref(b)) == 1
+    assert lib.polylla_batch_create(16, 16, 16, 16, 16, 2, 8, None, ctypes.byref(b)) == 1
+    assert lib.polylla_batch_create(20, 16, 16, 16, 16, 2, 0, None, ctypes.byref(b)) == 1
+    assert lib.polylla_batch_run(None, 0, None) == 1
+    assert lib.polylla_batch_tune(None, 1, None, None, None) == 1
+    assert lib.polylla_batch_destroy(None) == 1
+    k = lib.polylla_batch_schedules()
+    assert k >= 2
+    cap, thr = ctypes.c_int(), ctypes.c_int()
+    for s in range(k):
+        assert lib.polylla_batch_schedule_info(s, ctypes.byref(cap), ctypes.byref(thr)) == 0
+        assert cap.value in (16, 32, 48, 64) and thr.value % 32 == 0
+    assert lib.polylla_batch_schedule_info(k, ctypes.byref(cap), ctypes.byref(thr)) == 1
+    assert lib.polylla_batch_schedule_info(-1, None, None) == 1
