@@ -316,6 +316,70 @@ def run_ours(args, dist: Dist) -> dict | None:
     return out
 
 
+def run_batched(args, dist: Dist) -> dict | None:
+    """The batched form: 4,096 meshes (point counts log-uniform in [200, 200,000],
+    uniform or Gaussian mixture per mesh) as one batch -- autotuned schedule, CUDA
+    graph replays, inputs resident -- against the plain per-mesh path (one
+    polylla_run per mesh on one stream) on every 8th mesh of the same batch."""
+    import numpy as np
+    import torch
+
+    import meshgen
+    import paper_2204_05438_gb300 as pg
+
+    dev = torch.device("cuda", dist.local_rank)
+    t0 = time.perf_counter()
+    plan = meshgen.batch_plan(args.batch_meshes, 2024 + dist.rank)
+    meshes = meshgen.batch(plan["ns"], plan["seeds"], plan["kinds"], plan["sides"])
+    cat = meshgen.concat(meshes)
+    gen_s = time.perf_counter() - t0
+    m = int(cat["tri_off"][-1])
+    stream = torch.cuda.current_stream(dev)
+    B = pg.batch_from_numpy(cat, device=str(dev), validate=True)
+    best, tune_ms = B.tune(reps=2)
+    for _ in range(args.warmup):
+        B.run()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    e0.record(stream)
+    for _ in range(args.batch_steps):
+        B.run()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    ms = dist.max(e0.elapsed_time(e1)) / args.batch_steps
+    st = B.stats()
+    B.close()
+
+    # plain path, one mesh at a time, on a sample of the same meshes
+    sample = list(range(0, len(meshes), 8))
+    plain_ms, plain_tri = 0.0, 0
+    for j in sample:
+        M = pg.from_numpy(meshes[j], device=str(dev), validate=False)
+        M.run(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        M.run(stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms += a.elapsed_time(b)
+        plain_tri += meshes[j]["tri"].shape[0]
+        M.close()
+    plain_tps = plain_tri / (plain_ms * 1e-3)
+    value = dist.world * m / (ms * 1e-3)
+    return {"meshes": len(meshes), "triangles": m, "points": int(cat["vtx_off"][-1]),
+            "ms_per_run": ms, "value": value, "unit": UNIT,
+            "schedule": best, "schedule_info": pg.batch_schedule_info(best),
+            "tune_ms": [round(t, 4) for t in tune_ms],
+            "plain": {"value": plain_tps, "unit": UNIT, "meshes": len(sample),
+                      "triangles": plain_tri, "ms": round(plain_ms, 3),
+                      "sample": "every 8th mesh of the batch, one polylla_run each"},
+            "batched_over_plain": value / dist.world / plain_tps,
+            "n_poly": st["n_poly"], "generation_s": round(gen_s, 1),
+            "graph": "CUDA graph per schedule, replayed"}
+
+
 def cpu_baseline(mesh_name: str, budget_s: float) -> dict:
     """The oracle as it stands, one host thread, on the full workload mesh (or a
     smaller mesh of the same distribution if the full one would exceed the budget)."""
@@ -382,6 +446,9 @@ def main():
     ap.add_argument("--kernel-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-meshes", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -391,6 +458,8 @@ def main():
             out = run_reference(args, dist)
         else:
             out = run_ours(args, dist)
+            if out is not None and not args.no_batch and args.kernel_steps > 0:
+                out["batched"] = run_batched(args, dist)
             if out is not None and dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
                 out["cpu_baseline"] = cpu_baseline(args.workload, 30.0)
         if out is not None and dist.rank == 0:
