@@ -282,6 +282,77 @@ polylla_status polylla_batch_stats(polylla_batch_t batch, polylla_stats* out);
 polylla_mesh_t polylla_batch_mesh(polylla_batch_t batch);
 polylla_status polylla_batch_destroy(polylla_batch_t batch);
 
+/*
+ * Capacity handles and asynchronous results (for callers that reuse device
+ * state across meshes, such as the server below).
+ *
+ * polylla_mesh_footprint: device bytes a handle for n vertices and m triangles
+ * allocates (owns_inputs != 0: also its input arrays, as polylla_mesh_create_host
+ * does); -1 for invalid sizes.  No device call.
+ * polylla_mesh_set_size: for a handle created by polylla_mesh_create_host, the
+ * size of the next mesh (at most its creation sizes); the phases restart.
+ * polylla_mesh_inputs: the device input arrays of such a handle, to fill
+ * (asynchronously) before polylla_run.
+ * polylla_get_polygons_async: like polylla_get_polygons without synchronising:
+ * the latest CSR's device pointers, plus d_counts (int64[2]: n_poly, n_vtx) and
+ * d_error (the handle's int32 device error word, 0 if none), valid on the
+ * handle's stream once the phase that wrote them has run.
+ */
+int64_t polylla_mesh_footprint(int64_t n_vertices, int64_t n_tri, int owns_inputs);
+polylla_status polylla_mesh_set_size(polylla_mesh_t mesh, int64_t n_vertices, int64_t n_tri);
+polylla_status polylla_mesh_inputs(polylla_mesh_t mesh, int64_t** d_xy, int32_t** d_tri,
+                                   int32_t** d_twin);
+polylla_status polylla_get_polygons_async(polylla_mesh_t mesh, const int64_t** d_off,
+                                          const int32_t** d_vtx, const int64_t** d_counts,
+                                          const int32_t** d_error);
+
+/*
+ * Served form: a request loop with continuous batching (no counterpart in the
+ * paper).  polylla_server_create starts a worker thread on the current device
+ * with a device-memory budget (bytes, >= 1 MiB) and at most max_slots resident
+ * slots.  A slot is a capacity handle for a size class (the smallest power of two
+ * c >= max(4096, m, 2n) triangles, up to c/2 + 2 vertices) whose device state
+ * stays allocated and serves the next request of its class.
+ *
+ * polylla_server_submit queues one mesh (host arrays as for polylla_run_host;
+ * pinned memory lets the copies overlap) and returns its id.  h_off_out
+ * (int64[m+1]) and h_vtx_out (int32[3m]) receive the final CSR.  Every buffer
+ * must stay valid until the request completes.  Requests are admitted in arrival
+ * order as soon as a slot of their class is free or a new one fits the budget
+ * (idle slots of other classes are released to make room); a request whose class
+ * alone exceeds the budget completes with POLYLLA_ERR_OOM.  Admitted requests run
+ * on their slots' streams and overlap on the device; each is meshed by its own
+ * handle, so its result is the same as alone.
+ *
+ * polylla_server_poll moves up to `cap` completed results into out[], waiting up
+ * to wait_us microseconds for the first, and returns how many (-1 on bad
+ * arguments).  Times are seconds since the server's creation.
+ * polylla_server_info reports its state; polylla_server_destroy finishes every
+ * queued and running request, then frees everything.
+ */
+typedef struct polylla_server* polylla_server_t;
+typedef struct {
+  int64_t id;
+  int32_t status;   /* POLYLLA_OK, or the request's error */
+  int32_t reserved;
+  int64_t n_poly, n_vtx;
+  double submit_s, admit_s, done_s;
+} polylla_result;
+typedef struct {
+  int64_t slots, bytes_in_use, budget_bytes, pending, running, peak_running, completed;
+  double now_s;
+} polylla_server_stats;
+
+polylla_status polylla_server_create(int64_t budget_bytes, int max_slots, polylla_server_t* out);
+polylla_status polylla_server_submit(polylla_server_t server, const int64_t* h_xy,
+                                     int64_t n_vertices, const int32_t* h_tri,
+                                     const int32_t* h_twin, int64_t n_tri, int64_t* h_off_out,
+                                     int32_t* h_vtx_out, int64_t* id);
+int64_t polylla_server_poll(polylla_server_t server, polylla_result* out, int64_t cap,
+                            int64_t wait_us);
+polylla_status polylla_server_info(polylla_server_t server, polylla_server_stats* out);
+polylla_status polylla_server_destroy(polylla_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,21 @@ class PolyllaError(RuntimeError):
         self.code = code
 
 
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_poly", ctypes.c_int64), ("n_vtx", ctypes.c_int64), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("slots", "bytes_in_use", "budget_bytes", "pending",
+                                               "running", "peak_running", "completed")] + \
+               [("now_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n_seeds", "n_poly_trav", "n_vtx_trav", "n_tip_polygons", "n_tips", "n_splits",
@@ -103,6 +118,17 @@ def load_library(path: str | None = None):
             "polylla_batch_stats": ([vp, ctypes.POINTER(Stats)], st),
             "polylla_batch_mesh": ([vp], vp),
             "polylla_batch_destroy": ([vp], st),
+            "polylla_mesh_footprint": ([i64, i64, i32], i64),
+            "polylla_mesh_set_size": ([vp, i64, i64], st),
+            "polylla_mesh_inputs": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(vp)], st),
+            "polylla_get_polygons_async": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                            ctypes.POINTER(vp), ctypes.POINTER(vp)], st),
+            "polylla_server_create": ([i64, i32, ctypes.POINTER(vp)], st),
+            "polylla_server_submit": ([vp, vp, i64, vp, vp, i64, vp, vp, ctypes.POINTER(i64)], st),
+            "polylla_server_poll": ([vp, ctypes.POINTER(Result), i64, i64], i64),
+            "polylla_server_info": ([vp, ctypes.POINTER(ServerStats)], st),
+            "polylla_server_destroy": ([vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -360,6 +386,81 @@ def batch_destroy(batch: int):
     _check(load_library().polylla_batch_destroy(batch), "polylla_batch_destroy")
 
 
+def mesh_footprint(n_vertices: int, n_tri: int, owns_inputs: bool = False) -> int:
+    return int(load_library().polylla_mesh_footprint(n_vertices, n_tri, 1 if owns_inputs else 0))
+
+
+def mesh_set_size(mesh: int, n_vertices: int, n_tri: int):
+    _check(load_library().polylla_mesh_set_size(mesh, n_vertices, n_tri), "polylla_mesh_set_size")
+
+
+def mesh_inputs(mesh: int, n_vertices: int, n_tri: int):
+    """Views (xy int64 [2n], tri int32 [3m], twin int32 [3m]) of a host-created handle's
+    device inputs."""
+    a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load_library().polylla_mesh_inputs(mesh, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(c)), "polylla_mesh_inputs")
+    return (_view(a.value, 2 * n_vertices, "<i8", torch.int64),
+            _view(b.value, 3 * n_tri, "<i4", torch.int32),
+            _view(c.value, 3 * n_tri, "<i4", torch.int32))
+
+
+def get_polygons_async(mesh: int):
+    """Raw device pointers (off, vtx, counts[2], error) of the latest CSR, no sync."""
+    a, b, c, d = (ctypes.c_void_p() for _ in range(4))
+    _check(load_library().polylla_get_polygons_async(mesh, ctypes.byref(a), ctypes.byref(b),
+                                                     ctypes.byref(c), ctypes.byref(d)),
+           "polylla_get_polygons_async")
+    return a.value, b.value, c.value, d.value
+
+
+def server_create(budget_bytes: int, max_slots: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load_library().polylla_server_create(budget_bytes, max_slots, ctypes.byref(out)),
+           "polylla_server_create")
+    return out.value
+
+
+def _hptr(t: torch.Tensor, dtype: torch.dtype, name: str) -> int:
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host {dtype} tensor")
+    return t.data_ptr()
+
+
+def server_submit(server: int, xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
+                  off_out: torch.Tensor, vtx_out: torch.Tensor) -> int:
+    """Queue one mesh (host tensors, pinned for overlap; kept alive by the caller until
+    its result is polled); returns the request id."""
+    rid = ctypes.c_int64()
+    n, m = xy.numel() // 2, tri.numel() // 3
+    if off_out.numel() < m + 1 or vtx_out.numel() < 3 * m:
+        raise ValueError("output buffers need m + 1 offsets and 3m vertices")
+    _check(load_library().polylla_server_submit(
+        server, _hptr(xy, torch.int64, "xy"), n, _hptr(tri, torch.int32, "tri"),
+        _hptr(twin, torch.int32, "twin"), m, _hptr(off_out, torch.int64, "off_out"),
+        _hptr(vtx_out, torch.int32, "vtx_out"), ctypes.byref(rid)), "polylla_server_submit")
+    return rid.value
+
+
+def server_poll(server: int, cap: int = 256, wait_us: int = 0) -> list:
+    buf = (Result * cap)()
+    k = load_library().polylla_server_poll(server, buf, cap, wait_us)
+    if k < 0:
+        raise PolyllaError(1, "polylla_server_poll")
+    return [{f: getattr(buf[i], f) for f, _ in Result._fields_ if f != "reserved"}
+            for i in range(k)]
+
+
+def server_info(server: int) -> dict:
+    s = ServerStats()
+    _check(load_library().polylla_server_info(server, ctypes.byref(s)), "polylla_server_info")
+    return s.as_dict()
+
+
+def server_destroy(server: int):
+    _check(load_library().polylla_server_destroy(server), "polylla_server_destroy")
+
+
 # ------------------------------------------------------------------ convenience
 class Mesh:
     """Owns a handle over device tensors (kept alive here) and runs the phases."""
@@ -454,6 +555,50 @@ def batch_from_numpy(cat: dict, device: str = "cuda", validate: bool = True, str
     return Batch(dev(cat["xy"], torch.int64), dev(cat["vtx_off"], torch.int64),
                  dev(cat["tri"], torch.int32), dev(cat["twin"], torch.int32),
                  dev(cat["tri_off"], torch.int64), validate=validate, stream=stream)
+
+
+class Server:
+    """A server handle; keeps each request's host tensors alive until it is polled."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 32):
+        self.handle = server_create(budget_bytes, max_slots)
+        self.live = {}
+
+    def submit(self, xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
+               off_out: torch.Tensor | None = None, vtx_out: torch.Tensor | None = None) -> int:
+        m = tri.numel() // 3
+        pin = torch.cuda.is_available()
+        if off_out is None:
+            off_out = torch.empty(m + 1, dtype=torch.int64, pin_memory=pin)
+        if vtx_out is None:
+            vtx_out = torch.empty(3 * m, dtype=torch.int32, pin_memory=pin)
+        rid = server_submit(self.handle, xy, tri, twin, off_out, vtx_out)
+        self.live[rid] = (xy, tri, twin, off_out, vtx_out)
+        return rid
+
+    def poll(self, cap: int = 256, wait_us: int = 0) -> list:
+        """Completed results, each with its CSR (off, vtx) as host tensors."""
+        out = server_poll(self.handle, cap, wait_us)
+        for r in out:
+            _, _, _, off, vtx = self.live.pop(r["id"])
+            if r["status"] == 0:
+                r["off"] = off[:r["n_poly"] + 1]
+                r["vtx"] = vtx[:r["n_vtx"]]
+        return out
+
+    def info(self) -> dict:
+        return server_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_numpy(mesh: dict, device: str = "cuda", validate: bool = True, stream=None) -> Mesh:

@@ -30,6 +30,7 @@ struct TimingRec {
 
 struct polylla_mesh {
   DevMesh M;
+  long long n_cap = 0, m_cap = 0;  // sizes the buffers were allocated for
   int device = 0;
   int sms = 148;
   bool owns_inputs = false;
@@ -159,7 +160,13 @@ void free_all(polylla_mesh* h) {
   if (h->fork) cudaEventDestroy(h->fork);
 }
 
+// Device bytes of a handle's derived buffers for n vertices and m triangles (as
+// allocated by alloc_derived; each allocation rounded up to 512 bytes).
+long long derived_bytes(long long n, long long m);
+
 polylla_status alloc_derived(polylla_mesh* h) {
+  h->n_cap = h->M.n;
+  h->m_cap = h->M.m;
   const long long m = h->M.m, n = h->M.n;
   for (int k = 0; k < 2; ++k) {
     if (cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking) != cudaSuccess ||
@@ -217,6 +224,51 @@ polylla_status alloc_derived(polylla_mesh* h) {
   if (e == cudaSuccess) e = cudaMemset(h->vstamp, 0, sizeof(int) * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(h->C, 0, sizeof(Counters));
   return cuda_status(e);
+}
+
+long long derived_bytes(long long n, long long m) {
+  polylla_mesh c;  // only for the member types and capacities
+  const long long ntiles_tri = (m + kTriTile - 1) / kTriTile;
+  const long long ntiles_poly = (m + kPolyTile - 1) / kPolyTile;
+  const long long ntiles = ntiles_tri > ntiles_poly ? ntiles_tri : ntiles_poly;
+  c.F.cap = n + m;
+  c.pool.cap = 6 * m + 2 * n;
+  long long bytes = 0;
+#define COUNT(ptr, cnt) \
+  bytes += ((long long)sizeof(*(ptr)) * ((cnt) < 1 ? 1 : (long long)(cnt)) + 511) / 512 * 512
+  COUNT(c.lab, m + 4);
+  COUNT(c.seeds, m);
+  COUNT(c.succ, 3 * m);
+  COUNT(c.entry, m);
+  COUNT(c.tf, 3 * m);
+  COUNT(c.loc, 3 * m);
+  COUNT(c.vstamp, n);
+  COUNT(c.Lg.poly, m);
+  COUNT(c.Dl.poly, m);
+  COUNT(c.P.tip_h, m);
+  c.Dm.cap = m;
+  COUNT(c.Dm.poly, m);
+  COUNT(c.P.start, m);
+  COUNT(c.P.len, m);
+  COUNT(c.P.ntip, m);
+  COUNT(c.P.mode, m);
+  COUNT(c.P.pcnt, m);
+  COUNT(c.P.pbase, m);
+  COUNT(c.P.flen, m);
+  COUNT(c.P.pos, m);
+  COUNT(c.F.pos, c.F.cap);
+  COUNT(c.F.len, c.F.cap);
+  COUNT(c.F.h, c.F.cap);
+  COUNT(c.pool.v, c.pool.cap);
+  COUNT(c.tile_sum, 2 * ntiles);
+  COUNT(c.tile_off, 2 * ntiles);
+  COUNT(c.off_trav, m + 1);
+  COUNT(c.vtx_trav, 3 * m);
+  COUNT(c.off_final, m + 1);
+  COUNT(c.vtx_final, 3 * m);
+  COUNT(c.C, 1);
+#undef COUNT
+  return bytes;
 }
 
 polylla_status read_counters(polylla_mesh* h, Counters* out) {
@@ -715,6 +767,51 @@ int64_t polylla_kernel_times(polylla_mesh_t h, const char** names, float* ms, in
 }
 
 int64_t polylla_launch_count(polylla_mesh_t h) { return h ? h->launches : -1; }
+
+int64_t polylla_mesh_footprint(int64_t n_vertices, int64_t n_tri, int owns_inputs) {
+  if (n_vertices < 3 || n_tri < 1) return -1;
+  long long b = derived_bytes(n_vertices, n_tri);
+  if (owns_inputs) b += 16 * n_vertices + 24 * n_tri;
+  return b;
+}
+
+polylla_status polylla_mesh_set_size(polylla_mesh_t h, int64_t n_vertices, int64_t n_tri) {
+  POLY_TRY(check_handle(h));
+  if (!h->owns_inputs) return POLYLLA_ERR_STATE;
+  if (n_vertices < 3 || n_tri < 1 || n_vertices > h->n_cap || n_tri > h->m_cap)
+    return POLYLLA_ERR_INVALID_ARG;
+  h->M.n = n_vertices;
+  h->M.m = n_tri;
+  h->phase = kCreated;
+  h->latest_csr = -1;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_mesh_inputs(polylla_mesh_t h, int64_t** d_xy, int32_t** d_tri,
+                                   int32_t** d_twin) {
+  POLY_TRY(check_handle(h));
+  if (!d_xy || !d_tri || !d_twin) return POLYLLA_ERR_INVALID_ARG;
+  if (!h->owns_inputs) return POLYLLA_ERR_STATE;
+  *d_xy = reinterpret_cast<int64_t*>(const_cast<long long*>(h->M.xy));
+  *d_tri = const_cast<int32_t*>(h->M.tri);
+  *d_twin = const_cast<int32_t*>(h->M.twin);
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_get_polygons_async(polylla_mesh_t h, const int64_t** d_off,
+                                          const int32_t** d_vtx, const int64_t** d_counts,
+                                          const int32_t** d_error) {
+  POLY_TRY(check_handle(h));
+  if (!d_off || !d_vtx || !d_counts || !d_error) return POLYLLA_ERR_INVALID_ARG;
+  if (h->latest_csr < 0) return POLYLLA_ERR_STATE;
+  *d_off = reinterpret_cast<const int64_t*>(h->latest_csr == 1 ? h->off_final : h->off_trav);
+  *d_vtx = h->latest_csr == 1 ? h->vtx_final : h->vtx_trav;
+  static_assert(offsetof(Counters, n_vtx) == offsetof(Counters, n_poly) + sizeof(long long),
+                "n_poly and n_vtx are adjacent");
+  *d_counts = reinterpret_cast<const int64_t*>(&h->C->n_poly);
+  *d_error = &h->C->error;
+  return POLYLLA_OK;
+}
 
 polylla_status polylla_batch_create(const int64_t* d_xy, const int64_t* d_vtx_off,
                                     const int32_t* d_tri, const int32_t* d_twin,

@@ -91,3 +91,21 @@ def test_batch_argument_errors_need_no_device():
         assert cap.value in (16, 32, 48, 64) and thr.value % 32 == 0
     assert lib.polylla_batch_schedule_info(k, ctypes.byref(cap), ctypes.byref(thr)) == 1
     assert lib.polylla_batch_schedule_info(-1, None, None) == 1
+
+
+def test_server_argument_errors_need_no_device():
+    lib = pg.load_library()
+    s = ctypes.c_void_p(123)
+    assert lib.polylla_server_create(1 << 30, 4, None) == 1
+    assert lib.polylla_server_create(10, 4, ctypes.byref(s)) == 1
+    assert s.value is None
+    assert lib.polylla_server_create(1 << 30, 0, ctypes.byref(s)) == 1
+    rid = ctypes.c_int64()
+    assert lib.polylla_server_submit(None, None, 3, None, None, 1, None, None, ctypes.byref(rid)) == 1
+    assert lib.polylla_server_poll(None, None, 1, 0) == -1
+    assert lib.polylla_server_info(None, None) == 1
+    assert lib.polylla_server_destroy(None) == 1
+    assert lib.polylla_mesh_footprint(2, 1, 0) == -1
+    a = lib.polylla_mesh_footprint(1000, 2000, 0)
+    b = lib.polylla_mesh_footprint(1000, 2000, 1)
+    assert 0 < a < b and b - a == 16 * 1000 + 24 * 2000
