@@ -181,6 +181,13 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def aggregate(dist: Dist, units: int, steps: int, local_ms: float):
+    """Whole-job figure over replicas: the slowest rank's time, every rank's units.
+    Returns (ms per step, units per second)."""
+    total_ms = dist.max(local_ms)
+    return total_ms / steps, dist.world * units * steps / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, dist: Dist) -> dict | None:
     import numpy as np
@@ -219,9 +226,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     local_ms = e0.elapsed_time(e1)
     launches = pg.launch_count(M.handle) - launches0
     clk = clocks.stop()
-    total_ms = dist.max(local_ms)
-    ms_per_step = total_ms / args.steps
-    value = dist.world * m * args.steps / (total_ms / 1e3)
+    ms_per_step, value = aggregate(dist, m, args.steps, local_ms)
 
     # per-kernel durations: the same steps with events around every launch
     if args.kernel_steps <= 0:
@@ -492,10 +497,10 @@ def run_reference(args, dist: Dist) -> dict | None:
     if dist.rank != 0:
         return None
     cfg = meshgen.CONFIGS[args.workload]
-    per_step = max(0.05, 120.0 / max(1, args.steps + args.warmup))
-    sec_per_tri = 1.0 / 1.2e6  # oracle throughput measured on the full workload
+    per_step = max(0.01, args.ref_seconds / max(1, args.steps + args.warmup))
+    sec_per_tri = 1.0 / 2.4e6  # oracle throughput measured on the full workload (one Arm core)
     tri_target = per_step / sec_per_tri
-    n_sample = int(min(cfg["n"], max(2_000, tri_target / 2)))
+    n_sample = int(min(cfg["n"], max(500, tri_target / 2)))
     mesh = meshgen.generate(cfg["kind"], n_sample, cfg["side"], cfg["seed"])
     m = mesh["tri"].shape[0]
     for _ in range(args.warmup):
@@ -531,6 +536,8 @@ def main():
     ap.add_argument("--kernel-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="reference arm: host time of warm-up + steps, which sizes its sample")
     ap.add_argument("--batch-meshes", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-batch", action="store_true")
