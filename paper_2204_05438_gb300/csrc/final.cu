@@ -125,9 +125,18 @@ __global__ void __launch_bounds__(kBlock) k_final_write(PolyArrays P, FinalPiece
       const long long d0 = __shfl_sync(0xffffffffu, vb, a);
       const long long s1 = __shfl_sync(0xffffffffu, src + l, e - 1);
       const long long run = s1 - s0;
-      const int* from = pool.v + s0;
-      int* to = vtx + d0;
-      for (long long k = lane; k < run; k += 32) to[k] = from[k];
+      const int* __restrict__ from = pool.v + s0;
+      int* __restrict__ to = vtx + d0;
+      // up to four loads in flight per lane before their stores
+      for (long long k = lane; k < run; k += 128) {
+        int v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k + 32 * u < run) v[u] = from[k + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k + 32 * u < run) to[k + 32 * u] = v[u];
+      }
     }
   }
 }
