@@ -393,6 +393,15 @@ def run_batched(args, dist: Dist) -> dict | None:
     dist.barrier()
     ms = dist.max(e0.elapsed_time(e1)) / args.batch_steps
     st = B.stats()
+    # one run with per-kernel events (eager: timing bypasses the graphs)
+    hm = pg.batch_mesh(B.handle)
+    pg.set_timing(hm, True)
+    B.run(best)
+    recs = pg.kernel_times(hm, reset=True)
+    pg.set_timing(hm, False)
+    kern = {}
+    for name, t in recs:
+        kern[name] = round(kern.get(name, 0.0) + t, 4)
     B.close()
 
     # plain path, one mesh at a time, on a sample of the same meshes
@@ -419,7 +428,8 @@ def run_batched(args, dist: Dist) -> dict | None:
                       "triangles": plain_tri, "ms": round(plain_ms, 3),
                       "sample": "every 8th mesh of the batch, one polylla_run each"},
             "batched_over_plain": value / dist.world / plain_tps,
-            "n_poly": st["n_poly"], "generation_s": round(gen_s, 1),
+            "n_poly": st["n_poly"], "stats": st, "kernels_ms": kern,
+            "generation_s": round(gen_s, 1),
             "graph": "CUDA graph per schedule, replayed"}
 
 

@@ -244,8 +244,10 @@ polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64_t n_vertic
  * replayed afterwards.  schedule: 0 .. polylla_batch_schedules()-1, or
  * POLYLLA_SCHEDULE_TUNED for the one polylla_batch_tune picked (tuning first if
  * needed).  A schedule sets the longest polygon walked by one thread (longer
- * ones go to one thread block each) and that block's size;
- * polylla_batch_schedule_info reports both.
+ * ones go to one thread block each) and how those blocks are sized (long_mode 0:
+ * one large block per polygon; 1: small blocks first, several per SM, handing
+ * the regions they cannot hold to large ones); polylla_batch_schedule_info
+ * reports both.
  *
  * polylla_batch_tune times every schedule on this batch (`reps` graph replays
  * each, after one warm-up), stores the fastest, and returns it in *best and the
@@ -269,7 +271,7 @@ polylla_status polylla_batch_create(const int64_t* d_xy, const int64_t* d_vtx_of
                                     const int64_t* d_tri_off, int64_t n_meshes, uint32_t flags,
                                     void* stream, polylla_batch_t* out);
 int polylla_batch_schedules(void);
-polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_threads);
+polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_mode);
 polylla_status polylla_batch_tune(polylla_batch_t batch, int reps, void* stream, int* best,
                                   float* ms);
 polylla_status polylla_batch_run(polylla_batch_t batch, int schedule, void* stream);

@@ -328,7 +328,7 @@ def batch_schedule_info(schedule: int) -> dict:
     _check(load_library().polylla_batch_schedule_info(schedule, ctypes.byref(cap),
                                                       ctypes.byref(thr)),
            "polylla_batch_schedule_info")
-    return {"walk_cap": cap.value, "long_threads": thr.value}
+    return {"walk_cap": cap.value, "long_mode": thr.value}
 
 
 def batch_tune(batch: int, reps: int = 3, stream=None):

@@ -51,6 +51,7 @@ struct polylla_mesh {
   FinalPieces F{};
   Pool pool{};
   LongList Dm{};          // polygons with several tips
+  LongList Lg2{};         // long polygons the small blocks hand to the large ones
   int epoch = 0;
   long long* tile_sum = nullptr;
   long long* tile_off = nullptr;
@@ -65,9 +66,9 @@ struct polylla_mesh {
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 
-  // schedule: the walk's thread-per-seed cap and the long-polygon block size
+  // schedule: the walk's thread-per-seed cap and the long-polygon mode
   int walk_cap = kWalkCap;
-  int long_threads = 512;
+  int long_mode = 0;
   long long* obase = nullptr;  // batches: output index of each traversal polygon
 
   bool timing = false;
@@ -140,7 +141,7 @@ void free_all(polylla_mesh* h) {
                   h->P.pos,    h->F.pos,     h->F.len,     h->F.h,        h->pool.v,
                   h->tile_sum, h->tile_off,  h->off_trav,  h->vtx_trav,   h->off_final,
                   h->vtx_final, h->C,         h->Dl.poly,   h->P.tip_h,
-                  h->Dm.poly,   h->entry};
+                  h->Dm.poly,   h->entry,     h->Lg2.poly};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_inputs) {
@@ -200,6 +201,8 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->P.tip_h, m);
   h->Dm.cap = m;
   ALLOC(h->Dm.poly, m);
+  h->Lg2.cap = m;
+  ALLOC(h->Lg2.poly, m);
   ALLOC(h->P.start, m);
   ALLOC(h->P.len, m);
   ALLOC(h->P.ntip, m);
@@ -352,9 +355,9 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
     s2 = h->side[1];
   }
   POLY_TRY(launch(h, "long", s1, [&] {
-    return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg,
-                       h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->long_threads, h->C,
-                       2 * h->sms, s1);
+    return launch_long(M, h->lab, h->tf, h->seeds, h->succ, h->P, h->F, h->pool, h->Lg, h->Lg2,
+                       h->loc, h->vstamp, 2 * h->epoch + repair, repair, h->long_mode, h->C,
+                       h->sms, s1);
   }));
   if (repair) {
     POLY_TRY(launch(h, "repair_multi", s2, [&] {
@@ -414,10 +417,11 @@ polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags) {
 }
 
 // ---------------------------------------------------------------- batches
-// Schedules a batch can be run with (walk cap, long-polygon block threads).
+// Schedules a batch can be run with: the walk's thread-per-seed cap, and the
+// long-polygon mode (0: large blocks only; 1: small blocks first).
 constexpr int kSchedules = 4;
-constexpr int kSchedCap[kSchedules] = {64, 32, 48, 64};
-constexpr int kSchedLong[kSchedules] = {512, 512, 512, 256};
+constexpr int kSchedCap[kSchedules] = {64, 64, 32, 48};
+constexpr int kSchedLong[kSchedules] = {0, 1, 1, 1};
 
 }  // namespace
 
@@ -476,7 +480,7 @@ polylla_status batch_body(polylla_batch* b, cudaStream_t s) {
 polylla_status batch_run_sched(polylla_batch* b, int k, cudaStream_t s) {
   polylla_mesh* h = b->mesh;
   h->walk_cap = kSchedCap[k];
-  h->long_threads = kSchedLong[k];
+  h->long_mode = kSchedLong[k];
   b->pfirst_valid = false;
   if (h->timing) return batch_body(b, s);
   if (!b->exec[k]) {
@@ -894,10 +898,10 @@ polylla_status polylla_batch_create(const int64_t* d_xy, const int64_t* d_vtx_of
 
 int polylla_batch_schedules(void) { return kSchedules; }
 
-polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_threads) {
+polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_mode) {
   if (schedule < 0 || schedule >= kSchedules) return POLYLLA_ERR_INVALID_ARG;
   if (walk_cap) *walk_cap = kSchedCap[schedule];
-  if (long_threads) *long_threads = kSchedLong[schedule];
+  if (long_mode) *long_mode = kSchedLong[schedule];
   return POLYLLA_OK;
 }
 

@@ -31,23 +31,33 @@
 
 namespace polylla {
 
+// Two sizes of the block: a large one (4096 members, 4096 triangles, 512 threads,
+// about 180 KB of shared memory: one block per SM) for any region, and a small
+// one (512 members, 512 triangles, 128 threads, about 22 KB: several blocks per
+// SM) that hands a region it cannot hold to the large one.
 constexpr int kLongThreads = 512;
 constexpr int kLM = 4096;  // members of one long polygon (with its split half-edges)
 constexpr int kLT = 4096;  // BFS queue: triangles of one long region
-constexpr int kLongSmemInts = kLT + 10 * kLM;
-constexpr int kHashBits = 13;  // visited-triangle table of the search: 2 * kLM slots
-constexpr int kHashSlots = 1 << kHashBits;
-static_assert(kHashSlots == 2 * kLM, "the table spans two member buffers");
+constexpr int kSmallThreads = 128;
+constexpr int kSmallLM = 512;
+constexpr int kSmallLT = 512;
 
-// Insert triangle t into the block's visited table (open addressing, -1 = empty).
-// Returns 1 if t was new, 0 if it was there, -1 if the table is full.
+template <int LM, int LT>
+constexpr int long_smem_ints() { return LT + 10 * LM; }
+
+// Insert triangle t into the block's visited table of 2 * LM slots (open
+// addressing, -1 = empty).  Returns 1 if t was new, 0 if it was there, -1 if the
+// table is full.
+template <int LM>
 __device__ __forceinline__ int visit_insert(int* tab, int t) {
-  unsigned slot = ((unsigned)t * 2654435761u) >> (32 - kHashBits);
-  for (int probe = 0; probe < kHashSlots; ++probe) {
+  constexpr int kSlots = 2 * LM;
+  static_assert((kSlots & (kSlots - 1)) == 0, "a power of two");
+  unsigned slot = ((unsigned)t * 2654435761u) & (kSlots - 1);
+  for (int probe = 0; probe < kSlots; ++probe) {
     const int old = atomicCAS(tab + slot, -1, t);
     if (old == -1) return 1;
     if (old == t) return 0;
-    slot = (slot + 1) & (kHashSlots - 1);
+    slot = (slot + 1) & (kSlots - 1);
   }
   return -1;
 }
@@ -197,13 +207,20 @@ __device__ void long_fallback(const DevMesh& M, uint8_t* lab, int* tf, int t0, l
   atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)(cnt - 1));
 }
 
-__global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* lab, int* tf,
-                                                       const int* __restrict__ seeds,
-                                                       const int* __restrict__ succ, PolyArrays P,
-                                                       FinalPieces F, Pool pool, LongList Lg,
-                                                       int* __restrict__ loc,
-                                                       int* __restrict__ vstamp, int epoch,
-                                                       int repair, Counters* C) {
+// Lg / n: the polygons of this launch.  over (nullable): where a polygon too large
+// for this block size goes (with the counter n_over) instead of the sequential path.
+template <int THREADS, int LM, int LT>
+__global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, int* tf,
+                                                  const int* __restrict__ seeds,
+                                                  const int* __restrict__ succ, PolyArrays P,
+                                                  FinalPieces F, Pool pool, LongList Lg,
+                                                  const long long* n_list, LongList over,
+                                                  long long* n_over, int* __restrict__ loc,
+                                                  int* __restrict__ vstamp, int epoch, int repair,
+                                                  Counters* C) {
+  constexpr int kLM = LM;
+  constexpr int kLT = LT;
+  constexpr int kHashSlots = 2 * LM;
   extern __shared__ int smem[];
   int* RQ = smem;       // BFS queue; later the chord list and ordering counts
   int* mem = RQ + kLT;  // members
@@ -222,7 +239,7 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
   __shared__ long long s_base, s_fbase;
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
-  const long long nl = min(C->n_long, Lg.cap);
+  const long long nl = min(*n_list, Lg.cap);
   for (long long j = blockIdx.x; j < nl; j += gridDim.x) {
     const long long i = Lg.poly[j];
     const int t0 = seeds[i];
@@ -236,7 +253,7 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
       s_nm = 0;
       s_over = 0;
       RQ[0] = t0;
-      visit_insert(vis, t0);
+      visit_insert<LM>(vis, t0);
     }
     __syncthreads();
     for (;;) {
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
             s_over = 2;
           } else {
             const int nb = x / 3;
-            const int ins = visit_insert(vis, nb);
+            const int ins = visit_insert<LM>(vis, nb);
             if (ins > 0) {
               const int p = atomicAdd(&s_tail, 1);
               if (p < kLT) RQ[p] = nb;
@@ -274,8 +291,16 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
     const int L = s_nm;
     if (s_over) {
       if (threadIdx.x == 0) {
-        if (s_over == 2) set_error(C, POLYLLA_ERR_LIMIT, 106);
-        long_fallback(M, lab, tf, t0, i, P, F, pool, repair, C);
+        if (s_over == 2) {
+          set_error(C, POLYLLA_ERR_LIMIT, 106);
+        } else if (over.poly) {  // too large for this block: the large blocks take it
+          const long long q =
+              (long long)atomicAdd(reinterpret_cast<unsigned long long*>(n_over), 1ull);
+          if (q < over.cap) over.poly[q] = (int)i;
+          else set_error(C, POLYLLA_ERR_LIMIT, 113);
+        } else {
+          long_fallback(M, lab, tf, t0, i, P, F, pool, repair, C);
+        }
       }
       __syncthreads();
       continue;
@@ -369,7 +394,7 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
     // ---- 4b. which tips are split: in increasing tip order, a tip is removed when
     //          a split tip with a smaller id ends its split edge on it
     int* sb = R8;          // tip vertices, sorted
-    int* st = R8 + 2048;   // their tip indices (nt <= kLM / 2)
+    int* st = R8 + kLM / 2;  // their tip indices (nt <= kLM / 2)
     int* cx = R2;          // sorted index of the larger tip at each split edge's end
     int* cancelled = R1;
     const bool sortable = !s_fail && 2 * nt <= kLM;
@@ -429,8 +454,17 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
     const int ns = s_ns;
     const int N = L + 2 * ns;
     if (s_fail || N > kLM) {
-      // sequential path (no split edge has been marked yet)
-      if (threadIdx.x == 0) long_fallback(M, lab, tf, t0, i, P, F, pool, repair, C);
+      // no split edge has been marked yet: the large blocks, or the sequential path
+      if (threadIdx.x == 0) {
+        if (over.poly && !s_fail) {
+          const long long q =
+              (long long)atomicAdd(reinterpret_cast<unsigned long long*>(n_over), 1ull);
+          if (q < over.cap) over.poly[q] = (int)i;
+          else set_error(C, POLYLLA_ERR_LIMIT, 113);
+        } else {
+          long_fallback(M, lab, tf, t0, i, P, F, pool, repair, C);
+        }
+      }
       __syncthreads();
       continue;
     }
@@ -607,20 +641,45 @@ __global__ void __launch_bounds__(kLongThreads, 1) k_long(DevMesh M, uint8_t* la
   }
 }
 
-cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
-                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                        const LongList& Lg, int* loc, int* vstamp, int epoch,
-                        int repair, int threads, Counters* C, int grid, cudaStream_t s) {
-  if (threads < 128 || threads > kLongThreads || threads % 32) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(int) * (size_t)kLongSmemInts;
+template <int THREADS, int LM, int LT>
+cudaError_t launch_long_t(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds,
+                          const int* succ, const PolyArrays& P, const FinalPieces& F,
+                          const Pool& pool, const LongList& Lg, const long long* n_list,
+                          const LongList& over, long long* n_over, int* loc, int* vstamp,
+                          int epoch, int repair, Counters* C, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(int) * (size_t)long_smem_ints<LM, LT>();
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_long<THREADS, LM, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr = true;
   }
-  k_long<<<grid, threads, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg, loc,
-                                          vstamp, epoch, repair, C);
+  static int cap = 0;
+  grid = resident_grid(reinterpret_cast<const void*>(k_long<THREADS, LM, LT>), THREADS, smem,
+                       grid, &cap);
+  k_long<THREADS, LM, LT><<<grid, THREADS, smem, s>>>(M, lab, tf, seeds, succ, P, F, pool, Lg,
+                                                      n_list, over, n_over, loc, vstamp, epoch,
+                                                      repair, C);
   return cudaGetLastError();
+}
+
+cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
+                        const PolyArrays& P, const FinalPieces& F, const Pool& pool,
+                        const LongList& Lg, const LongList& Lg2, int* loc, int* vstamp, int epoch,
+                        int repair, int mode, Counters* C, int sms, cudaStream_t s) {
+  const LongList none{nullptr, 0};
+  if (mode == 0)  // large blocks only
+    return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg,
+                                                 &C->n_long, none, nullptr, loc, vstamp, epoch,
+                                                 repair, C, sms, s);
+  // small blocks first; the regions they cannot hold, in large blocks
+  cudaError_t e = launch_long_t<kSmallThreads, kSmallLM, kSmallLT>(
+      M, lab, tf, seeds, succ, P, F, pool, Lg, &C->n_long, Lg2, &C->n_long2, loc, vstamp, epoch,
+      repair, C, 16 * sms, s);
+  if (e != cudaSuccess) return e;
+  return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg2,
+                                               &C->n_long2, none, nullptr, loc, vstamp, epoch,
+                                               repair, C, sms, s);
 }
 
 }  // namespace polylla

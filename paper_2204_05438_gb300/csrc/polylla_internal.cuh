@@ -42,6 +42,7 @@ struct Counters {
   long long n_defer;      // polygons with one tip, left to k_repair_one
   long long n_multi;      // polygons with several tips, left to k_repair_multi
   long long ticket;       // tile tickets of the single-pass (look-back) scans
+  long long n_long2;      // long polygons handed from the small blocks to the large ones
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
   int error;              // first device error (polylla_status), 0 if none
@@ -252,11 +253,13 @@ cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int
 cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                                 const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                                 const LongList& Dm, Counters* C, int sms, cudaStream_t s);
-// One block per long polygon: gather, rank and, if `repair`, split.
+// One block per long polygon: gather, rank and, if `repair`, split.  mode 0:
+// large blocks only; mode 1: small blocks first, the regions they cannot hold
+// (listed in Lg2) then in large blocks.
 cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                        const LongList& Lg, int* loc, int* vstamp, int epoch,
-                        int repair, int threads, Counters* C, int grid, cudaStream_t s);
+                        const LongList& Lg, const LongList& Lg2, int* loc, int* vstamp, int epoch,
+                        int repair, int mode, Counters* C, int sms, cudaStream_t s);
 // Output: the CSR offsets (a look-back scan over `status`, zeroed, one word per
 // 256-polygon tile) and the copy; also C->n_poly, C->n_vtx and off[n_poly].
 // obase (nullable): per traversal polygon, the index of its first output polygon.

@@ -88,7 +88,7 @@ def test_batch_argument_errors_need_no_device():
     cap, thr = ctypes.c_int(), ctypes.c_int()
     for s in range(k):
         assert lib.polylla_batch_schedule_info(s, ctypes.byref(cap), ctypes.byref(thr)) == 0
-        assert cap.value in (16, 32, 48, 64) and thr.value % 32 == 0
+        assert cap.value in (16, 32, 48, 64) and thr.value in (0, 1)
     assert lib.polylla_batch_schedule_info(k, ctypes.byref(cap), ctypes.byref(thr)) == 1
     assert lib.polylla_batch_schedule_info(-1, None, None) == 1
 
