@@ -218,3 +218,113 @@ def check_final_mesh(mesh, polys, frontier_final):
     assert sorted(directed) == expect, "polygon edges differ from the frontier half-edges"
     undirected = {tuple(sorted(e)) for e in directed}
     assert n - len(undirected) + len(polys) == 1, "Euler characteristic"
+
+
+# ------------------------------------------------------------------ brute-force repair
+def brute_final_polygons(mesh):
+    """The final polygonal mesh from the definitions, by recursion on triangle sets
+    (Section 3.2.3 with readings #9 and #11): a polygon is the boundary of a set of
+    triangles joined across non-frontier edges; while a polygon has a barrier-edge
+    tip, take the tip with the smallest vertex id, mark the middle internal edge at
+    it (the ceil(k/2)-th of the k internal edges met ccw after the barrier edge)
+    frontier, split the triangle set into its connected components, and repair the
+    component on the tip->x side first, then the other.  Polygons in ascending seed
+    order, each from its smallest (origin, half-edge).  Written for tiny meshes: it
+    recomputes components after every split instead of tracking rounds."""
+    b = brute_labels(mesh)
+    fr = list(b["frontier"])
+    tri = [tuple(map(int, t)) for t in mesh["tri"]]
+    twin = [int(g) for g in mesh["twin"]]
+    m = len(tri)
+
+    def nxt(h):
+        return 3 * (h // 3) + (h % 3 + 1) % 3
+
+    def prv(h):
+        return 3 * (h // 3) + (h % 3 + 2) % 3
+
+    def org(h):
+        return tri[h // 3][h % 3]
+
+    def components(tris):
+        parent = {t: t for t in tris}
+
+        def find(x):
+            while parent[x] != x:
+                parent[x] = parent[parent[x]]
+                x = parent[x]
+            return x
+
+        for t in tris:
+            for k in range(3):
+                h = 3 * t + k
+                g = twin[h]
+                if g >= 0 and not fr[h] and (g // 3) in parent:
+                    ra, rb = find(t), find(g // 3)
+                    if ra != rb:
+                        parent[ra] = rb
+        out = {}
+        for t in tris:
+            out.setdefault(find(t), set()).add(t)
+        return list(out.values())
+
+    def boundary_cycle(tris):
+        hs = [3 * t + k for t in tris for k in range(3) if fr[3 * t + k]]
+        h0 = min(hs, key=lambda h: (org(h), h))
+        cyc, h = [], h0
+        while True:
+            cyc.append(h)
+            g = nxt(h)
+            while not fr[g]:
+                g = nxt(twin[g])
+            h = g
+            if h == h0:
+                break
+            assert len(cyc) <= 3 * m
+        assert sorted(cyc) == sorted(hs), "a region boundary is not one cycle"
+        return cyc
+
+    def repair(tris):
+        cyc = boundary_cycle(tris)
+        n = len(cyc)
+        verts = [org(h) for h in cyc]
+        cand = [(verts[i], cyc[(i - 1) % n]) for i in range(n)
+                if n > 2 and verts[(i - 1) % n] == verts[(i + 1) % n]]
+        if not cand:
+            return [verts]
+        b_tip, p = min(cand)           # smallest tip vertex; p = a->b
+        o0 = twin[p]                   # b->a, the barrier half-edge leaving the tip
+        internal, o = [], twin[prv(o0)]
+        while o != o0:
+            assert not fr[o], "a tip with a second frontier edge"
+            internal.append(o)
+            o = twin[prv(o)]
+        k = len(internal)
+        assert k >= 2
+        oj = internal[(k + 1) // 2 - 1]  # e_ceil(k/2), 1-based
+        fr[oj] = fr[twin[oj]] = 1
+        parts = components(tris)
+        assert len(parts) == 2
+        first = next(p for p in parts if oj // 3 in p)
+        second = next(p for p in parts if p is not first)
+        return repair(first) + repair(second)
+
+    regions = components(set(range(m)))
+    by_tri = {}
+    for r in regions:
+        for t in r:
+            by_tri[t] = r
+    polys = []
+    for t in range(m):
+        if b["seed"][t]:
+            polys += repair(by_tri[t])
+    return polys, fr
+
+
+def tip_order_meshes():
+    """Meshes on which the order of the tips matters: the polygons differ when the
+    largest tip is split first instead of the smallest (found by search over seeded
+    generator meshes; the smallest has 25 triangles)."""
+    return [meshgen.generate("gmm", 16, 1 << 10, 18 * 7919 + 16),
+            meshgen.generate("gmm", 60, 1 << 10, 32 * 7919 + 60),
+            meshgen.generate("uniform", 60, 1 << 10, 52 * 7919 + 60)]

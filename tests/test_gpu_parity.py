@@ -235,3 +235,13 @@ def test_launch_count_and_timing():
     assert pg.launch_count(M.handle) - before == len(times) >= 6
     assert all(ms >= 0 for _, ms in times)
     M.close()
+
+
+def test_tip_order_meshes():
+    """Meshes on which the order of the tips changes the polygons."""
+    from meshlib import tip_order_meshes
+    for mesh in tip_order_meshes():
+        ref = oracle.run(mesh)
+        off, vtx, lab, _ = gpu_run(mesh)[0]
+        np.testing.assert_array_equal(off, ref["off"])
+        np.testing.assert_array_equal(vtx, ref["vtx"])

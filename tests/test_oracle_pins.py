@@ -12,8 +12,8 @@ import pytest
 
 import meshgen
 import oracle
-from meshlib import (brute_labels, brute_regions, check_final_mesh, csr_to_lists, golden_cases,
-                     grid_mesh, lepp_end, tips)
+from meshlib import (brute_final_polygons, brute_labels, brute_regions, check_final_mesh,
+                     csr_to_lists, golden_cases, grid_mesh, lepp_end, tip_order_meshes, tips)
 
 GOLDEN = golden_cases()
 
@@ -23,6 +23,17 @@ def _halfedges(flags):
 
 
 # --------------------------------------------------------------------- pin suite
+def pin_repair_bruteforce(mesh, lib=None):
+    """The oracle's final polygons and final frontier against the recursive
+    brute-force repair (smallest tip first, middle internal edge, connected
+    components after every split)."""
+    r = oracle.run(mesh, lib)
+    polys, fr = brute_final_polygons(mesh)
+    assert csr_to_lists(r["off"], r["vtx"]) == polys
+    assert r["frontier"].tolist() == fr
+
+
+TIP_ORDER = tip_order_meshes()
 def pin_golden(case, lib=None):
     e = case["expect"]
     r = oracle.full(case["mesh"], lib)
@@ -112,6 +123,18 @@ def test_bruteforce_tiny(idx):
     pin_bruteforce(TINY[idx])
 
 
+@pytest.mark.parametrize("idx", range(len(TIP_ORDER)))
+def test_repair_bruteforce_tip_order(idx):
+    """Meshes on which splitting the largest tip first gives other polygons: the
+    oracle's rounds must give exactly the recursive brute force's polygons."""
+    pin_repair_bruteforce(TIP_ORDER[idx])
+
+
+def test_repair_bruteforce_small():
+    for s in range(12):
+        pin_repair_bruteforce(meshgen.generate("gmm", 120, 1 << 12, 500 + s))
+
+
 def test_bruteforce_small_with_tips():
     """Small Delaunay meshes that do have barrier-edge tips: brute-force labels and
     regions, then every final-mesh invariant after reparation."""
@@ -175,6 +198,8 @@ MUTATIONS = {
     "longest_is_shortest": ("if (edge_longer(xy, tri, twin, 3 * t + k, 3 * t + best)) best = k;",
                             "if (edge_longer(xy, tri, twin, 3 * t + best, 3 * t + k)) best = k;"),
     "length_dx_only": ("return dx * dx + dy * dy;", "return dx * dx + dy;"),
+    "tip_largest_first": ("if (va == vc && (tip < 0 || vb < tip)) {",
+                          "if (va == vc && (tip < 0 || vb > tip)) {"),
 }
 
 
@@ -196,6 +221,11 @@ def _run_pins(lib):
             pin_bruteforce(mesh, lib)
         except Exception:
             failed.append(f"tiny{i}")
+    for i, mesh in enumerate(TIP_ORDER):
+        try:
+            pin_repair_bruteforce(mesh, lib)
+        except Exception:
+            failed.append(f"tiporder{i}")
     return failed
 
 
