@@ -221,6 +221,73 @@ def concat(meshes: list) -> dict:
             "vtx_off": vtx_off, "tri_off": tri_off}
 
 
+def twin_fast(tri) -> np.ndarray:
+    """twin_from_tri by sorting (for large meshes); raises on a directed edge used twice."""
+    tri = np.asarray(tri, dtype=np.int64).reshape(-1, 3)
+    org = tri.reshape(-1)
+    dst = tri[:, [1, 2, 0]].reshape(-1)
+    n = int(tri.max()) + 1 if tri.size else 1
+    key = org * n + dst
+    order = np.argsort(key, kind="stable")
+    sk = key[order]
+    if sk.size > 1 and np.any(sk[1:] == sk[:-1]):
+        raise ValueError("a directed edge is used twice")
+    rev = dst * n + org
+    pos = np.searchsorted(sk, rev)
+    pos = np.minimum(pos, sk.size - 1)
+    hit = sk[pos] == rev
+    twin = np.full(org.size, -1, dtype=np.int32)
+    twin[hit] = order[pos[hit]].astype(np.int32)
+    return twin
+
+
+def carve(mesh: dict, keep) -> dict:
+    """The sub-mesh of the triangles whose centroid satisfies keep(cx, cy) (arrays),
+    made a manifold domain -- triangles around a vertex where boundaries pinch are
+    dropped until none is left -- with unused vertices removed (ids renumbered in
+    order) and twins rebuilt.  For non-convex domains and domains with holes."""
+    xy = np.asarray(mesh["xy"], dtype=np.int64).reshape(-1, 2)
+    tri = np.asarray(mesh["tri"], dtype=np.int64).reshape(-1, 3)
+    c = xy[tri].sum(axis=1) / 3.0
+    tri = tri[keep(c[:, 0], c[:, 1])]
+    for _ in range(64):
+        if tri.shape[0] == 0:
+            break
+        twin = twin_fast(tri)
+        org = tri.reshape(-1)
+        bnd = org[twin < 0]
+        cnt = np.bincount(bnd, minlength=xy.shape[0])
+        bad = cnt > 1  # two boundary edges leave the vertex: boundaries pinch there
+        if not bad.any():
+            break
+        tri = tri[~bad[tri].any(axis=1)]
+    used = np.zeros(xy.shape[0], dtype=bool)
+    used[tri.reshape(-1)] = True
+    remap = np.cumsum(used) - 1
+    tri2 = remap[tri].astype(np.int32)
+    return {"xy": np.ascontiguousarray(xy[used]), "tri": np.ascontiguousarray(tri2),
+            "twin": twin_fast(tri2)}
+
+
+def domain_with_holes(kind: str, n: int, side: int, seed: int, holes: int = 6) -> dict:
+    """A non-convex domain with holes: the Delaunay mesh of n seeded points, minus
+    an L-shaped notch (the corner x > 0.6 side, y > 0.55 side) and `holes` disks at
+    seeded centres (radius 4-9 % of the side)."""
+    mesh = generate(kind, n, side, seed)
+    rng = np.random.default_rng(seed + 1)
+    cx = rng.uniform(0.1, 0.9, holes) * side
+    cy = rng.uniform(0.1, 0.9, holes) * side
+    r = rng.uniform(0.04, 0.09, holes) * side
+
+    def keep(x, y):
+        k = ~((x > 0.6 * side) & (y > 0.55 * side))
+        for i in range(holes):
+            k &= (x - cx[i]) ** 2 + (y - cy[i]) ** 2 > r[i] ** 2
+        return k
+
+    return carve(mesh, keep)
+
+
 def twin_from_tri(tri) -> np.ndarray:
     """Half-edge twin array of a triangle list (for hand-built meshes).
 

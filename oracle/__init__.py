@@ -73,6 +73,8 @@ def _bind(path: str):
     lib.oracle_repair.restype = i64
     lib.oracle_run.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp]
     lib.oracle_run.restype = i64
+    lib.oracle_lepp.argtypes = [vp, i64, vp, vp, vp]
+    lib.oracle_lepp.restype = i64
     return lib
 
 
@@ -124,6 +126,19 @@ def seeds(lab: dict, lib=None) -> np.ndarray:
     out = np.zeros(max(seed.shape[0], 1), np.int32)
     ns = lib.oracle_seed_list(_p(seed), seed.shape[0], _p(out))
     return out[:ns].copy()
+
+
+def lepp(mesh, max_edge: np.ndarray, lib=None):
+    """Per triangle the seed of the terminal edge its longest-edge propagation path
+    reaches, and the path's length (links).  Returns (region int32[m], depth int32[m])."""
+    lib = lib or _load()
+    _, tri, twin = _mesh_arrays(mesh)
+    m = tri.shape[0]
+    max_edge = np.ascontiguousarray(max_edge, dtype=np.uint8)
+    region = np.zeros(m, np.int32)
+    depth = np.zeros(m, np.int32)
+    _check(lib.oracle_lepp(_p(twin), m, _p(max_edge), _p(region), _p(depth)))
+    return region, depth
 
 
 def traverse(mesh, frontier: np.ndarray, seed_list: np.ndarray, lib=None):

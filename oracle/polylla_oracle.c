@@ -126,6 +126,41 @@ int oracle_label_frontier(const int32_t* twin, int64_t m, const uint8_t* max_edg
 }
 
 /* The seed triangles in ascending order (the Seed array read front to back). */
+/*
+ * Longest-edge propagation paths (the Lepp that defines terminal-edge regions,
+ * Section 2; Lepp kernels are the paper's future work, Section 5).  From triangle t,
+ * follow the neighbour across the longest edge until that edge is the longest
+ * edge of both its triangles, or a border edge -- a terminal edge.  region[t] is
+ * the seed of the terminal edge reached (its lower triangle, or the border
+ * triangle itself); depth[t] is the number of links followed.  Returns the largest
+ * depth, or ORACLE_ERR_NOT_DISK if a path runs longer than m links.
+ */
+int64_t oracle_lepp(const int32_t* twin, int64_t m, const uint8_t* max_edge, int32_t* region,
+                    int32_t* depth) {
+  if (!twin || !max_edge || !region || !depth || m < 1) return ORACLE_ERR_ARG;
+  int64_t deepest = 0;
+  for (int64_t t = 0; t < m; ++t) {
+    int64_t u = t, d = 0;
+    for (;;) {
+      const int64_t h = 3 * u + max_edge[u];
+      const int64_t g = twin[h];
+      if (g < 0) {  /* border terminal edge */
+        region[t] = (int32_t)u;
+        break;
+      }
+      if (is_longest(max_edge, g)) {  /* longest of both triangles */
+        region[t] = (int32_t)(u < g / 3 ? u : g / 3);
+        break;
+      }
+      u = g / 3;
+      if (++d > m) return ORACLE_ERR_NOT_DISK;
+    }
+    depth[t] = (int32_t)d;
+    if (d > deepest) deepest = d;
+  }
+  return deepest;
+}
+
 int64_t oracle_seed_list(const uint8_t* seed, int64_t m, int32_t* seeds) {
   int64_t ns = 0;
   for (int64_t t = 0; t < m; ++t)

@@ -24,6 +24,8 @@ int oracle_label_seed(const int32_t* twin, int64_t m, const uint8_t* max_edge, u
 int oracle_label_frontier(const int32_t* twin, int64_t m, const uint8_t* max_edge,
                           uint8_t* frontier);
 int64_t oracle_seed_list(const uint8_t* seed, int64_t m, int32_t* seeds);
+int64_t oracle_lepp(const int32_t* twin, int64_t m, const uint8_t* max_edge, int32_t* region,
+                    int32_t* depth);
 int64_t oracle_traverse(const int32_t* tri, const int32_t* twin, int64_t m, const uint8_t* frontier,
                         const int32_t* seeds, int64_t ns, int64_t* off, int32_t* vtx,
                         int64_t cap_vtx);

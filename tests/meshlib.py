@@ -189,11 +189,13 @@ def tips(poly):
     return [poly[(i + 1) % n] for i in range(n) if poly[i] == poly[(i + 2) % n]]
 
 
-def check_final_mesh(mesh, polys, frontier_final):
+def check_final_mesh(mesh, polys, frontier_final, convex=True):
     """Invariants of the final polygonal mesh (Section 3.2.3's output): every
-    polygon simple, ccw, with positive area; areas add up to the domain (hull)
-    area; the polygons' edges are exactly the frontier edges (each frontier
-    half-edge in exactly one polygon); every vertex is used; Euler V - E + F = 1."""
+    polygon simple, ccw, with positive area; areas add up to the domain's area (the
+    triangles' total, which is the hull's for a convex domain); the polygons' edges
+    are exactly the frontier edges (each frontier half-edge in exactly one
+    polygon); every vertex is used; the Euler characteristic V - E + F is the
+    triangulation's (1 for a disk, 1 - h with h holes)."""
     xy = mesh["xy"]
     tri = mesh["tri"]
     n = xy.shape[0]
@@ -208,7 +210,10 @@ def check_final_mesh(mesh, polys, frontier_final):
         tot += a
         used.update(p)
         directed += [(p[i], p[(i + 1) % len(p)]) for i in range(len(p))]
-    assert tot == hull_twice_area(xy), "areas do not sum to the domain area"
+    tri_area = sum(twice_area(list(map(int, t)), xy) for t in tri)
+    assert tot == tri_area, "areas do not sum to the domain area"
+    if convex:
+        assert tot == hull_twice_area(xy), "areas do not sum to the hull area"
     assert used == set(range(n)), "vertex set changed"
     assert len(directed) == len(set(directed)), "a half-edge is in two polygons"
     org = tri.reshape(-1)
@@ -217,7 +222,9 @@ def check_final_mesh(mesh, polys, frontier_final):
     expect = sorted(zip(org[fr].tolist(), dst[fr].tolist()))
     assert sorted(directed) == expect, "polygon edges differ from the frontier half-edges"
     undirected = {tuple(sorted(e)) for e in directed}
-    assert n - len(undirected) + len(polys) == 1, "Euler characteristic"
+    tri_edges = {tuple(sorted((int(a), int(b)))) for a, b in zip(org.tolist(), dst.tolist())}
+    chi = n - len(tri_edges) + tri.shape[0]
+    assert n - len(undirected) + len(polys) == chi, "Euler characteristic"
 
 
 # ------------------------------------------------------------------ brute-force repair

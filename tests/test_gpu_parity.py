@@ -245,3 +245,10 @@ def test_tip_order_meshes():
         off, vtx, lab, _ = gpu_run(mesh)[0]
         np.testing.assert_array_equal(off, ref["off"])
         np.testing.assert_array_equal(vtx, ref["vtx"])
+
+
+@pytest.mark.parametrize("n,kind,seed", [(300, "uniform", 1), (3000, "gmm", 2), (200_000, "gmm", 3)])
+def test_domain_with_holes(n, kind, seed):
+    """Non-convex domains with holes: border edges inside the hull."""
+    mesh = meshgen.domain_with_holes(kind, n, 1 << 20, seed)
+    assert_parity(mesh)

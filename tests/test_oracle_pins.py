@@ -63,7 +63,7 @@ def pin_grid(k, seed, lib=None):
     assert int(fr.sum()) == 3 * m - 2 * k * k
 
 
-def pin_bruteforce(mesh, lib=None):
+def pin_bruteforce(mesh, lib=None, convex=True):
     r = oracle.full(mesh, lib)
     b = brute_labels(mesh)
     lab = r["label"]
@@ -86,7 +86,7 @@ def pin_bruteforce(mesh, lib=None):
         assert edges == bnd[comp[s]], "polygon is not the region boundary"
         assert p[0] == min(p), "polygon does not start at its smallest vertex"
     final = csr_to_lists(r["off"], r["vtx"])
-    check_final_mesh(mesh, final, r["frontier_final"])
+    check_final_mesh(mesh, final, r["frontier_final"], convex=convex)
     assert len(final) == len(polys) + r["splits"]
     assert len(r["vtx"]) == len(r["trav_vtx"]) + 2 * r["splits"]
     return r
@@ -170,6 +170,24 @@ def test_invariants_gmm_20k():
     assert len(final) == len(r["seeds"]) + r["splits"]
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_domain_with_holes_bruteforce(seed):
+    """Non-convex domains with holes (border edges inside the hull): brute-force
+    labels, regions and repair, and every final-mesh invariant with the domain's
+    area and Euler characteristic."""
+    mesh = meshgen.domain_with_holes("gmm" if seed % 2 else "uniform", 300, 1 << 16, 40 + seed)
+    pin_bruteforce(mesh, convex=False)
+    pin_repair_bruteforce(mesh)
+
+
+def test_domain_with_holes_invariants_20k():
+    mesh = meshgen.domain_with_holes("gmm", 20_000, 1 << 20, 9)
+    r = oracle.full(mesh)
+    final = csr_to_lists(r["off"], r["vtx"])
+    check_final_mesh(mesh, final, r["frontier_final"], convex=False)
+    assert len(final) == len(r["seeds"]) + r["splits"]
+
+
 def test_run_matches_phases():
     mesh = meshgen.load("uniform-1k")
     a = oracle.full(mesh)
@@ -200,6 +218,9 @@ MUTATIONS = {
     "length_dx_only": ("return dx * dx + dy * dy;", "return dx * dx + dy;"),
     "tip_largest_first": ("if (va == vc && (tip < 0 || vb < tip)) {",
                           "if (va == vc && (tip < 0 || vb > tip)) {"),
+    "lepp_upper_seed": ("region[t] = (int32_t)(u < g / 3 ? u : g / 3);",
+                        "region[t] = (int32_t)(u < g / 3 ? g / 3 : u);"),
+    "lepp_depth_from_one": ("int64_t u = t, d = 0;", "int64_t u = t, d = 1;"),
 }
 
 
@@ -226,6 +247,11 @@ def _run_pins(lib):
             pin_repair_bruteforce(mesh, lib)
         except Exception:
             failed.append(f"tiporder{i}")
+    for i, mesh in enumerate(TINY[:10]):
+        try:
+            pin_lepp(mesh, lib)
+        except Exception:
+            failed.append(f"lepp{i}")
     return failed
 
 
@@ -244,3 +270,42 @@ def test_planted_mistake_is_caught(name, tmp_path):
 
 def test_unmutated_oracle_passes_pin_suite():
     assert _run_pins(None) == []
+
+
+# --------------------------------------------------------------------- LEPP
+def pin_lepp(mesh, lib=None):
+    """Longest-edge propagation paths: each triangle's path ends at the terminal
+    edge the brute force reaches; the region it names is the triangle's connected
+    component across non-frontier edges (and that component's seed); depth is 0
+    exactly on the terminal edges' triangles and one more than the next triangle's
+    elsewhere."""
+    b = brute_labels(mesh)
+    region, depth = oracle.lepp(mesh, np.asarray(b["max_edge"], np.uint8), lib)
+    comp, _ = brute_regions(mesh, b["frontier"])
+    ends = lepp_end(mesh, b["max_edge"])
+    twin = mesh["twin"]
+    seed_of = {}
+    for t in range(len(comp)):
+        if b["seed"][t]:
+            seed_of[comp[t]] = t
+    for t in range(len(comp)):
+        assert region[t] == seed_of[comp[t]]
+        assert ends[t] == ends[region[t]]
+        h = 3 * t + b["max_edge"][t]
+        g = int(twin[h])
+        on_terminal = g < 0 or b["max_edge"][g // 3] == g % 3
+        if on_terminal:
+            assert depth[t] == 0
+        else:
+            assert depth[t] == depth[g // 3] + 1
+
+
+@pytest.mark.parametrize("idx", range(0, 60, 6))
+def test_lepp_tiny(idx):
+    pin_lepp(TINY[idx])
+
+
+def test_lepp_small_and_holes():
+    for s in range(4):
+        pin_lepp(meshgen.generate("gmm", 400, 1 << 16, 900 + s))
+        pin_lepp(meshgen.domain_with_holes("uniform", 400, 1 << 16, 950 + s))
