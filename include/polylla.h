@@ -220,6 +220,23 @@ polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64_t n_vertic
                                            int64_t* d_n_seeds, void* stream);
 
 /*
+ * Longest-edge propagation paths (Section 2's Lepp, which defines terminal-edge
+ * regions; Lepp-based kernels are the paper's future work, Section 5), from the
+ * label phase's Max array.  For every triangle t, following the neighbour across
+ * the longest edge until that edge is terminal (the longest edge of both its
+ * triangles, or a border edge): region[t] is the seed of the terminal edge reached
+ * (its lower triangle, or the border triangle) -- the seed of t's terminal-edge
+ * region -- and depth[t] the number of links followed.
+ * polylla_lepp: after polylla_label (any later phase keeps the Max array);
+ * asynchronous.  polylla_get_lepp (synchronises, reports a path error): device
+ * int32[m] arrays owned by the handle, valid until the next polylla_label or
+ * destroy; POLYLLA_ERR_STATE before polylla_lepp.
+ */
+polylla_status polylla_lepp(polylla_mesh_t mesh, void* stream);
+polylla_status polylla_get_lepp(polylla_mesh_t mesh, const int32_t** d_region,
+                                const int32_t** d_depth);
+
+/*
  * Batches: many independent meshes in one run (the paper meshes one
  * triangulation at a time; this form has no counterpart there).
  *

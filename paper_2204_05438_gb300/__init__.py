@@ -129,6 +129,8 @@ def load_library(path: str | None = None):
             "polylla_server_poll": ([vp, ctypes.POINTER(Result), i64, i64], i64),
             "polylla_server_info": ([vp, ctypes.POINTER(ServerStats)], st),
             "polylla_server_destroy": ([vp], st),
+            "polylla_lepp": ([vp, vp], st),
+            "polylla_get_lepp": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -299,6 +301,18 @@ def label_seeds_noalloc(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
         _dptr(twin, torch.int32, "twin"), m, _dptr(lab_out, torch.uint8, "lab_out"),
         _dptr(seeds_out, torch.int32, "seeds_out"), _dptr(n_seeds_out, torch.int64, "n_seeds_out"),
         _stream(stream)), "polylla_label_seeds_noalloc")
+
+
+def lepp(mesh: int, stream=None):
+    _check(load_library().polylla_lepp(mesh, _stream(stream)), "polylla_lepp")
+
+
+def get_lepp(mesh: int, m: int):
+    """Views (region int32 [m], depth int32 [m]) of the longest-edge paths."""
+    a, b = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load_library().polylla_get_lepp(mesh, ctypes.byref(a), ctypes.byref(b)),
+           "polylla_get_lepp")
+    return _view(a.value, m, "<i4", torch.int32), _view(b.value, m, "<i4", torch.int32)
 
 
 SCHEDULE_TUNED = -1
@@ -494,6 +508,10 @@ class Mesh:
 
     def polygons(self):
         return get_polygons(self.handle)
+
+    def lepp(self, stream=None):
+        lepp(self.handle, stream)
+        return get_lepp(self.handle, self.m)
 
     def stats(self) -> dict:
         return get_stats(self.handle)

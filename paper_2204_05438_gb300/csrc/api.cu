@@ -41,6 +41,8 @@ struct polylla_mesh {
   uint8_t* lab = nullptr;
   int* seeds = nullptr;
   int* entry = nullptr;   // per seed: entry half-edge of its region (or -1 - t)
+  int* lepp_region = nullptr;  // per triangle: seed of its longest-edge path's end
+  int* lepp_depth = nullptr;   // per triangle: links of that path
   int* succ = nullptr;    // per frontier half-edge: boundary successor | tip flag
   int* tf = nullptr;      // twin | frontier bit, per half-edge (written by the label phase)
   int* loc = nullptr;     // per half-edge: member index inside a long-polygon block
@@ -69,6 +71,7 @@ struct polylla_mesh {
   // schedule: the walk's thread-per-seed cap and the long-polygon mode
   int walk_cap = kWalkCap;
   int long_mode = 0;
+  bool lepp_valid = false;
   long long* obase = nullptr;  // batches: output index of each traversal polygon
 
   bool timing = false;
@@ -141,7 +144,8 @@ void free_all(polylla_mesh* h) {
                   h->P.pos,    h->F.pos,     h->F.len,     h->F.h,        h->pool.v,
                   h->tile_sum, h->tile_off,  h->off_trav,  h->vtx_trav,   h->off_final,
                   h->vtx_final, h->C,         h->Dl.poly,   h->P.tip_h,
-                  h->Dm.poly,   h->entry,     h->Lg2.poly};
+                  h->Dm.poly,   h->entry,     h->Lg2.poly,
+                  h->lepp_region, h->lepp_depth};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_inputs) {
@@ -193,6 +197,8 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->seeds, m);
   ALLOC(h->succ, 3 * m);
   ALLOC(h->entry, m);
+  ALLOC(h->lepp_region, m);
+  ALLOC(h->lepp_depth, m);
   ALLOC(h->tf, 3 * m);
   ALLOC(h->loc, 3 * m);
   ALLOC(h->vstamp, n);
@@ -309,6 +315,7 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
     return launch_label_class(M, h->lab, h->tile_sum, h->tf, h->C, g2, s);
   }));
   h->phase = kLabeled;
+  h->lepp_valid = false;
   h->latest_csr = -1;
   return POLYLLA_OK;
 }
@@ -772,6 +779,31 @@ int64_t polylla_kernel_times(polylla_mesh_t h, const char** names, float* ms, in
 
 int64_t polylla_launch_count(polylla_mesh_t h) { return h ? h->launches : -1; }
 
+polylla_status polylla_lepp(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  if (h->phase < kLabeled) return POLYLLA_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  const int g = grid_for(h, h->M.m, kBlock);
+  POLY_TRY(launch(h, "lepp", s, [&] {
+    return launch_lepp(h->M, h->lab, h->lepp_region, h->lepp_depth, h->C, g, s);
+  }));
+  h->lepp_valid = true;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_get_lepp(polylla_mesh_t h, const int32_t** d_region,
+                                const int32_t** d_depth) {
+  POLY_TRY(check_handle(h));
+  if (!d_region || !d_depth) return POLYLLA_ERR_INVALID_ARG;
+  if (!h->lepp_valid) return POLYLLA_ERR_STATE;
+  Counters c;
+  POLY_TRY(read_counters(h, &c));  // syncs; reports a path error
+  *d_region = h->lepp_region;
+  *d_depth = h->lepp_depth;
+  return POLYLLA_OK;
+}
+
 int64_t polylla_mesh_footprint(int64_t n_vertices, int64_t n_tri, int owns_inputs) {
   if (n_vertices < 3 || n_tri < 1) return -1;
   long long b = derived_bytes(n_vertices, n_tri);
@@ -788,6 +820,7 @@ polylla_status polylla_mesh_set_size(polylla_mesh_t h, int64_t n_vertices, int64
   h->M.m = n_tri;
   h->phase = kCreated;
   h->latest_csr = -1;
+  h->lepp_valid = false;
   return POLYLLA_OK;
 }
 

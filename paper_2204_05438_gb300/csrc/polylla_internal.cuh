@@ -267,6 +267,9 @@ cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const 
                                unsigned long long* status, long long* off, int* vtx,
                                long long* obase, long long m, Counters* C, int grid,
                                cudaStream_t s);
+// Longest-edge propagation paths: per triangle its region's seed and the path length.
+cudaError_t launch_lepp(const DevMesh& M, const uint8_t* lab, int* region, int* depth, Counters* C,
+                        int grid, cudaStream_t s);
 // Batches: union ids from per-mesh local ids, and each mesh's first output polygon.
 cudaError_t launch_batch_globalize(const int* tri, const int* twin, const long long* tri_off,
                                    const long long* vtx_off, long long n_meshes, long long m,

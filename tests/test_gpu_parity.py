@@ -252,3 +252,33 @@ def test_domain_with_holes(n, kind, seed):
     """Non-convex domains with holes: border edges inside the hull."""
     mesh = meshgen.domain_with_holes(kind, n, 1 << 20, seed)
     assert_parity(mesh)
+
+
+@pytest.mark.parametrize("name", ["uniform-1k", "uniform-1m", "holes-20k", "tiny"])
+def test_lepp(name):
+    """Longest-edge paths: region seed and path length per triangle, bit-exact."""
+    if name == "holes-20k":
+        meshes = [meshgen.domain_with_holes("gmm", 20_000, 1 << 20, 7)]
+    elif name == "tiny":
+        meshes = [c["mesh"] for c in golden_cases()] + [grid_mesh(6, 2)[0]]
+    else:
+        meshes = [meshgen.load(name)]
+    for mesh in meshes:
+        lab = oracle.label(mesh)
+        ref_r, ref_d = oracle.lepp(mesh, lab["max_edge"])
+        M = pg.from_numpy(mesh)
+        M.label()
+        with pytest.raises(pg.PolyllaError):
+            pg.get_lepp(M.handle, M.m)  # before polylla_lepp
+        r, d = (t.cpu().numpy() for t in M.lepp())
+        M.seeds()  # the paths survive the later phases (they keep the Max array)
+        M.traverse()
+        M.repair()
+        r2, _ = (t.cpu().numpy() for t in pg.get_lepp(M.handle, M.m))
+        M.run()  # a new label phase: the paths must be asked for again
+        with pytest.raises(pg.PolyllaError):
+            pg.get_lepp(M.handle, M.m)
+        M.close()
+        np.testing.assert_array_equal(r, ref_r)
+        np.testing.assert_array_equal(d, ref_d)
+        np.testing.assert_array_equal(r2, ref_r)
