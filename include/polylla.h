@@ -98,13 +98,16 @@ typedef struct {
 
 /*
  * Create a handle over a device-resident triangulation (Section 2's arrays).
- * d_xy, d_tri, d_twin: device pointers as described above (borrowed).  d_twin
- * must not be NULL.  flags: 0 or POLYLLA_VALIDATE; with VALIDATE the mesh is
- * checked on the device (ids and twins in range, twin an involution between
- * reversed edges, coordinates in range, every triangle ccw with positive area)
- * and the call synchronises with `stream`.  Allocates every derived buffer
- * (about 60 bytes per triangle) so that later phases allocate nothing.
- * On success *out receives the handle; on failure *out is NULL.
+ * d_xy, d_tri, d_twin: device pointers as described above (borrowed).  d_twin may
+ * be NULL: the handle then builds the twin array from tri on the device (its
+ * Neighbor array comes from the triangulator in the paper, Section 2) and
+ * synchronises; a directed edge used twice or an edge with more than two
+ * triangles gives POLYLLA_ERR_TOPOLOGY.  flags: 0 or POLYLLA_VALIDATE; with
+ * VALIDATE the mesh is checked on the device (ids and twins in range, twin an
+ * involution between reversed edges, coordinates in range, every triangle ccw
+ * with positive area) and the call synchronises with `stream`.  Allocates every
+ * derived buffer (about 200 bytes per triangle) so that later phases allocate
+ * nothing.  On success *out receives the handle; on failure *out is NULL.
  */
 polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, const int32_t* d_tri,
                                    int64_t n_tri, const int32_t* d_twin, uint32_t flags,
@@ -172,14 +175,21 @@ const char* polylla_status_str(polylla_status status);
  * End-to-end call from HOST memory: copies xy, tri, twin from host buffers
  * (pinned memory recommended) into device buffers owned by `mesh`, runs
  * polylla_run, and copies the final CSR back into host buffers.  `mesh` must
- * have been created with polylla_mesh_create_host.  h_off needs room for
- * n_tri+1 entries and h_vtx for 3*n_tri (the bounds of the final mesh).
+ * have been created with polylla_mesh_create_host.  h_twin may be NULL: the twin
+ * array is then built on the device from tri (one copy less).  h_off needs room
+ * for n_tri+1 entries and h_vtx for 3*n_tri (the bounds of the final mesh).
  * Synchronises.
+ *
+ * polylla_mesh_build_twin: for a handle that owns its twin array (created with
+ * d_twin NULL, or by polylla_mesh_create_host), rebuilds it from the current tri
+ * on the device; asynchronous (errors at the next synchronising call); the
+ * phases restart.
  */
 polylla_status polylla_mesh_create_host(int64_t n_vertices, int64_t n_tri, polylla_mesh_t* out);
 polylla_status polylla_run_host(polylla_mesh_t mesh, const int64_t* h_xy, const int32_t* h_tri,
                                 const int32_t* h_twin, int64_t* h_off, int32_t* h_vtx,
                                 int64_t* n_poly, int64_t* n_vtx, void* stream);
+polylla_status polylla_mesh_build_twin(polylla_mesh_t mesh, void* stream);
 
 /*
  * Per-kernel timing: when enabled, every kernel the handle launches is bracketed
@@ -334,7 +344,8 @@ polylla_status polylla_get_polygons_async(polylla_mesh_t mesh, const int64_t** d
  * stays allocated and serves the next request of its class.
  *
  * polylla_server_submit queues one mesh (host arrays as for polylla_run_host;
- * pinned memory lets the copies overlap) and returns its id.  h_off_out
+ * pinned memory lets the copies overlap; h_twin NULL: built on the device) and
+ * returns its id.  h_off_out
  * (int64[m+1]) and h_vtx_out (int32[3m]) receive the final CSR.  Every buffer
  * must stay valid until the request completes.  Requests are admitted in arrival
  * order as soon as a slot of their class is free or a new one fits the budget

@@ -130,6 +130,7 @@ def load_library(path: str | None = None):
             "polylla_server_info": ([vp, ctypes.POINTER(ServerStats)], st),
             "polylla_server_destroy": ([vp], st),
             "polylla_lepp": ([vp, vp], st),
+            "polylla_mesh_build_twin": ([vp, vp], st),
             "polylla_get_lepp": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp)], st),
         }
         for name, (args, res) in sig.items():
@@ -176,16 +177,18 @@ def _view(ptr: int, n: int, typestr: str, dtype: torch.dtype) -> torch.Tensor:
 
 
 # ------------------------------------------------------------------ C-ABI mirror
-def mesh_create(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor, flags: int = VALIDATE,
-                stream=None) -> int:
-    """polylla_mesh_create: xy int64 [n,2], tri int32 [m,3], twin int32 [3m] on the GPU."""
+def mesh_create(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor | None,
+                flags: int = VALIDATE, stream=None) -> int:
+    """polylla_mesh_create: xy int64 [n,2], tri int32 [m,3], twin int32 [3m] on the GPU
+    (twin None: built on the device from tri)."""
     lib = load_library()
     n = xy.numel() // 2
     m = tri.numel() // 3
     h = ctypes.c_void_p()
+    tw = None if twin is None else _dptr(twin, torch.int32, "twin")
     _check(lib.polylla_mesh_create(_dptr(xy, torch.int64, "xy"), n, _dptr(tri, torch.int32, "tri"),
-                                   m, _dptr(twin, torch.int32, "twin"), flags, _stream(stream),
-                                   ctypes.byref(h)), "polylla_mesh_create")
+                                   m, tw, flags, _stream(stream), ctypes.byref(h)),
+           "polylla_mesh_create")
     return h.value
 
 
@@ -259,10 +262,11 @@ def run_host(mesh: int, xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
              off_out: torch.Tensor, vtx_out: torch.Tensor, stream=None):
     """polylla_run_host on (preferably pinned) CPU tensors; returns (n_poly, n_vtx)."""
     for t, name in ((xy, "xy"), (tri, "tri"), (twin, "twin"), (off_out, "off"), (vtx_out, "vtx")):
-        if t.is_cuda or not t.is_contiguous():
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
             raise ValueError(f"{name} must be a contiguous host tensor")
     npoly, nv = ctypes.c_int64(), ctypes.c_int64()
-    _check(load_library().polylla_run_host(mesh, xy.data_ptr(), tri.data_ptr(), twin.data_ptr(),
+    tw = None if twin is None else twin.data_ptr()
+    _check(load_library().polylla_run_host(mesh, xy.data_ptr(), tri.data_ptr(), tw,
                                            off_out.data_ptr(), vtx_out.data_ptr(),
                                            ctypes.byref(npoly), ctypes.byref(nv),
                                            _stream(stream)), "polylla_run_host")
@@ -301,6 +305,10 @@ def label_seeds_noalloc(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor,
         _dptr(twin, torch.int32, "twin"), m, _dptr(lab_out, torch.uint8, "lab_out"),
         _dptr(seeds_out, torch.int32, "seeds_out"), _dptr(n_seeds_out, torch.int64, "n_seeds_out"),
         _stream(stream)), "polylla_label_seeds_noalloc")
+
+
+def mesh_build_twin(mesh: int, stream=None):
+    _check(load_library().polylla_mesh_build_twin(mesh, _stream(stream)), "polylla_mesh_build_twin")
 
 
 def lepp(mesh: int, stream=None):
@@ -451,7 +459,8 @@ def server_submit(server: int, xy: torch.Tensor, tri: torch.Tensor, twin: torch.
         raise ValueError("output buffers need m + 1 offsets and 3m vertices")
     _check(load_library().polylla_server_submit(
         server, _hptr(xy, torch.int64, "xy"), n, _hptr(tri, torch.int32, "tri"),
-        _hptr(twin, torch.int32, "twin"), m, _hptr(off_out, torch.int64, "off_out"),
+        None if twin is None else _hptr(twin, torch.int32, "twin"), m,
+        _hptr(off_out, torch.int64, "off_out"),
         _hptr(vtx_out, torch.int32, "vtx_out"), ctypes.byref(rid)), "polylla_server_submit")
     return rid.value
 

@@ -34,6 +34,10 @@ struct polylla_mesh {
   int device = 0;
   int sms = 148;
   bool owns_inputs = false;
+  bool owns_twin = false;      // twin built on the device (handle-owned)
+  int* tw_cnt = nullptr;       // twin construction scratch: per-vertex counts,
+  int* tw_start = nullptr;     // first slots (n + 1),
+  int* tw_adj = nullptr;       // outgoing half-edges (3m)
   int phase = kCreated;
   int latest_csr = -1;  // 0: traversal CSR, 1: final CSR
   cudaStream_t last_stream = nullptr;
@@ -147,6 +151,9 @@ void free_all(polylla_mesh* h) {
                   h->Dm.poly,   h->entry,     h->Lg2.poly,
                   h->lepp_region, h->lepp_depth};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->owns_twin && !h->owns_inputs) cudaFree(const_cast<int*>(h->M.twin));
+  for (int* p : {h->tw_cnt, h->tw_start, h->tw_adj})
     if (p) cudaFree(p);
   if (h->owns_inputs) {
     cudaFree(const_cast<long long*>(h->M.xy));
@@ -408,11 +415,39 @@ polylla_status do_repair(polylla_mesh* h, cudaStream_t s) {
   return POLYLLA_OK;
 }
 
+// Scratch of the twin construction, for handles that may build their twin.
+polylla_status alloc_twin_scratch(polylla_mesh* h) {
+  const long long m = h->M.m, n = h->M.n;
+  const long long have = (m + kPolyTile - 1) / kPolyTile;  // tile words allocated
+  if ((n + kTriTile - 1) / kTriTile > have) return POLYLLA_ERR_INVALID_ARG;
+  cudaError_t e = dalloc(&h->tw_cnt, n);
+  if (e == cudaSuccess) e = dalloc(&h->tw_start, n + 1);
+  if (e == cudaSuccess) e = dalloc(&h->tw_adj, 3 * m);
+  return cuda_status(e);
+}
+
+polylla_status do_build_twin(polylla_mesh* h, cudaStream_t s) {
+  if (!h->tw_adj || !(h->owns_twin || h->owns_inputs)) return POLYLLA_ERR_STATE;
+  h->phase = kCreated;
+  h->latest_csr = -1;
+  h->lepp_valid = false;
+  return launch(h, "build_twin", s, [&] {
+    return launch_build_twin(h->M.tri, h->M.m, h->M.n, const_cast<int*>(h->M.twin), h->tw_cnt,
+                             h->tw_start, h->tw_adj, h->tile_sum, h->tile_off, h->C, h->sms, s);
+  });
+}
+
 polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags) {
   if (cudaGetDevice(&h->device) != cudaSuccess) return POLYLLA_ERR_CUDA;
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   POLY_TRY(alloc_derived(h));
   h->last_stream = s;
+  if (h->owns_twin || h->owns_inputs) POLY_TRY(alloc_twin_scratch(h));
+  if (h->owns_twin) {  // built from tri now, and checked
+    POLY_TRY(do_build_twin(h, s));
+    Counters c;
+    POLY_TRY(read_counters(h, &c));
+  }
   if (flags & POLYLLA_VALIDATE) {
     const int g = grid_for(h, (h->M.n > 3 * h->M.m ? h->M.n : 3 * h->M.m), kBlock);
     POLY_TRY(launch(h, "validate", s, [&] { return launch_validate(h->M, h->C, g, s); }));
@@ -557,7 +592,7 @@ polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, cons
                                    void* stream, polylla_mesh_t* out) {
   if (!out) return POLYLLA_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!d_xy || !d_tri || !d_twin) return POLYLLA_ERR_INVALID_ARG;
+  if (!d_xy || !d_tri) return POLYLLA_ERR_INVALID_ARG;
   if (n_vertices < 3 || n_vertices >= kMaxVertices || n_tri < 1 || n_tri >= kMaxTriangles)
     return POLYLLA_ERR_INVALID_ARG;
   if ((flags & ~POLYLLA_VALIDATE) != 0) return POLYLLA_ERR_INVALID_ARG;
@@ -569,7 +604,14 @@ polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, cons
   h->M.twin = d_twin;
   h->M.n = n_vertices;
   h->M.m = n_tri;
-  polylla_status st = create_common(h, (cudaStream_t)stream, flags);
+  polylla_status st = POLYLLA_OK;
+  if (!d_twin) {  // built on the device from tri
+    int* tw = nullptr;
+    st = cuda_status(dalloc(&tw, 3 * n_tri));
+    h->M.twin = tw;
+    h->owns_twin = true;
+  }
+  if (st == POLYLLA_OK) st = create_common(h, (cudaStream_t)stream, flags);
   if (st != POLYLLA_OK) {
     free_all(h);
     delete h;
@@ -719,8 +761,7 @@ polylla_status polylla_run_host(polylla_mesh_t h, const int64_t* h_xy, const int
                                 int64_t* n_poly, int64_t* n_vtx, void* stream) {
   POLY_TRY(check_handle(h));
   if (!h->owns_inputs) return POLYLLA_ERR_STATE;
-  if (!h_xy || !h_tri || !h_twin || !h_off || !h_vtx || !n_poly || !n_vtx)
-    return POLYLLA_ERR_INVALID_ARG;
+  if (!h_xy || !h_tri || !h_off || !h_vtx || !n_poly || !n_vtx) return POLYLLA_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const long long n = h->M.n, m = h->M.m;
   cudaError_t e =
@@ -729,10 +770,11 @@ polylla_status polylla_run_host(polylla_mesh_t h, const int64_t* h_xy, const int
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(const_cast<int*>(h->M.tri), h_tri, sizeof(int) * 3 * m,
                         cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && h_twin)
     e = cudaMemcpyAsync(const_cast<int*>(h->M.twin), h_twin, sizeof(int) * 3 * m,
                         cudaMemcpyHostToDevice, s);
   POLY_TRY(cuda_status(e));
+  if (!h_twin) POLY_TRY(do_build_twin(h, s));  // from tri, on the device
   POLY_TRY(polylla_run(h, stream));
   Counters c;
   POLY_TRY(read_counters(h, &c));
@@ -807,8 +849,15 @@ polylla_status polylla_get_lepp(polylla_mesh_t h, const int32_t** d_region,
 int64_t polylla_mesh_footprint(int64_t n_vertices, int64_t n_tri, int owns_inputs) {
   if (n_vertices < 3 || n_tri < 1) return -1;
   long long b = derived_bytes(n_vertices, n_tri);
-  if (owns_inputs) b += 16 * n_vertices + 24 * n_tri;
+  if (owns_inputs) b += 16 * n_vertices + 24 * n_tri + 8 * n_vertices + 4 + 12 * n_tri;
   return b;
+}
+
+polylla_status polylla_mesh_build_twin(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  return do_build_twin(h, s);
 }
 
 polylla_status polylla_mesh_set_size(polylla_mesh_t h, int64_t n_vertices, int64_t n_tri) {

@@ -127,9 +127,10 @@ polylla_status start(Slot* s, const SReq& r) {
   cudaError_t e = cudaMemcpyAsync(xy, r.xy, sizeof(int64_t) * 2 * r.n, cudaMemcpyHostToDevice, s->s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(tri, r.tri, sizeof(int32_t) * 3 * r.m, cudaMemcpyHostToDevice, s->s);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && r.twin)
     e = cudaMemcpyAsync(twin, r.twin, sizeof(int32_t) * 3 * r.m, cudaMemcpyHostToDevice, s->s);
   if (e != cudaSuccess) return POLYLLA_ERR_CUDA;
+  if (!r.twin && (st = polylla_mesh_build_twin(s->h, s->s)) != POLYLLA_OK) return st;
   st = polylla_run(s->h, s->s);
   if (st != POLYLLA_OK) return st;
   const int64_t* off;
@@ -324,8 +325,7 @@ polylla_status polylla_server_create(int64_t budget_bytes, int max_slots, polyll
 polylla_status polylla_server_submit(polylla_server_t S, const int64_t* h_xy, int64_t n_vertices,
                                      const int32_t* h_tri, const int32_t* h_twin, int64_t n_tri,
                                      int64_t* h_off_out, int32_t* h_vtx_out, int64_t* id) {
-  if (!S || !h_xy || !h_tri || !h_twin || !h_off_out || !h_vtx_out || !id)
-    return POLYLLA_ERR_INVALID_ARG;
+  if (!S || !h_xy || !h_tri || !h_off_out || !h_vtx_out || !id) return POLYLLA_ERR_INVALID_ARG;
   if (n_vertices < 3 || n_tri < 1 || n_vertices >= ((int64_t)1 << 30) ||
       n_tri >= ((int64_t)1 << 29))
     return POLYLLA_ERR_INVALID_ARG;

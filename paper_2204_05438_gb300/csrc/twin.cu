@@ -1,0 +1,158 @@
+// The twin array from the triangles alone (the step before the paper's input: its
+// Neighbor array, Section 2, comes from the triangulator).  Half-edge h = 3t + k
+// runs from tri[h] to tri[3t + (k+1) % 3]; its twin is the half-edge running the
+// other way, or -1.
+//
+//   k_twin_count   outgoing half-edges per vertex (atomics), and the per-tile sums
+//                  of those counts for the tile scan;
+//   k_twin_start   each vertex's first slot: its tile's offset + an in-tile scan;
+//   k_twin_fill    every half-edge into its origin's slots;
+//   k_twin_match   h = u->v finds v->u among v's outgoing half-edges (about six
+//                  on a Delaunay mesh).  A directed edge used twice, or an edge
+//                  with more than two triangles, sets POLYLLA_ERR_TOPOLOGY.
+#include "polylla_internal.cuh"
+
+namespace polylla {
+
+constexpr int kTwinTile = kTriTile;  // vertices per tile of the count scan
+
+__global__ void __launch_bounds__(kBlock) k_twin_count(const int* __restrict__ tri, long long m,
+                                                       long long n, int* __restrict__ cnt,
+                                                       Counters* C) {
+  const long long H = 3 * m;
+  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
+       h += (long long)gridDim.x * blockDim.x) {
+    const int v = __ldg(tri + h);
+    if (v < 0 || v >= n) {
+      set_error(C, POLYLLA_ERR_RANGE, 140);
+      continue;
+    }
+    atomicAdd(cnt + v, 1);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_twin_tiles(const int* __restrict__ cnt, long long n,
+                                                       long long* __restrict__ tile_sum) {
+  __shared__ long long sh[kBlock / 32];
+  const long long ntiles = (n + kTwinTile - 1) / kTwinTile;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    long long s = 0;
+    for (int j = threadIdx.x; j < kTwinTile; j += kBlock) {
+      const long long v = tile * kTwinTile + j;
+      if (v < n) s += cnt[v];
+    }
+    const long long tot = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+      tile_sum[2 * tile] = tot;
+      tile_sum[2 * tile + 1] = 0;
+    }
+  }
+}
+
+// start[v] = first slot of v; start[n] = 3m.  cnt is cleared for the fill.
+__global__ void __launch_bounds__(kBlock) k_twin_start(int* __restrict__ cnt, long long n,
+                                                       const long long* __restrict__ tile_off,
+                                                       int* __restrict__ start, long long m) {
+  __shared__ long long sh[kBlock / 32];
+  constexpr int kPer = kTwinTile / kBlock;
+  const long long ntiles = (n + kTwinTile - 1) / kTwinTile;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long v0 = tile * kTwinTile + (long long)threadIdx.x * kPer;
+    int c[kPer];
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      c[j] = (v0 + j < n) ? cnt[v0 + j] : 0;
+      s += c[j];
+    }
+    long long tot;
+    long long p = tile_off[2 * tile] + block_exclusive_scan(s, &tot, sh);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (v0 + j < n) {
+        start[v0 + j] = (int)p;
+        cnt[v0 + j] = 0;
+      }
+      p += c[j];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[n] = (int)(3 * m);
+}
+
+__global__ void __launch_bounds__(kBlock) k_twin_fill(const int* __restrict__ tri, long long m,
+                                                      long long n, const int* __restrict__ start,
+                                                      int* __restrict__ cnt, int* __restrict__ adj) {
+  const long long H = 3 * m;
+  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
+       h += (long long)gridDim.x * blockDim.x) {
+    const int v = __ldg(tri + h);
+    if (v < 0 || v >= n) continue;
+    adj[start[v] + atomicAdd(cnt + v, 1)] = (int)h;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_twin_match(const int* __restrict__ tri, long long m,
+                                                       long long n, const int* __restrict__ start,
+                                                       const int* __restrict__ adj,
+                                                       int* __restrict__ twin, Counters* C) {
+  const long long H = 3 * m;
+  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
+       h += (long long)gridDim.x * blockDim.x) {
+    const int u = __ldg(tri + h);
+    const int v = __ldg(tri + he_next((int)h));
+    if (u < 0 || u >= n || v < 0 || v >= n) {
+      twin[h] = -1;
+      continue;
+    }
+    // the twin: v -> u among v's outgoing half-edges; a second v -> u, or a second
+    // u -> v among u's, is a non-manifold edge
+    int g = -1, hits = 0;
+    const int b0 = start[v], b1 = start[v + 1];
+    for (int q = b0; q < b1; ++q) {
+      const int x = adj[q];
+      if (__ldg(tri + he_next(x)) == u) {
+        g = x;
+        ++hits;
+      }
+    }
+    int same = 0;
+    const int a0 = start[u], a1 = start[u + 1];
+    for (int q = a0; q < a1; ++q) same += __ldg(tri + he_next(adj[q])) == v;
+    if (hits > 1 || same != 1) set_error(C, POLYLLA_ERR_TOPOLOGY, 141);
+    twin[h] = g;
+  }
+}
+
+cudaError_t launch_build_twin(const int* tri, long long m, long long n, int* twin, int* cnt,
+                              int* start, int* adj, long long* tile_sum, long long* tile_off,
+                              Counters* C, int sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n, s);
+  if (e != cudaSuccess) return e;
+  static int c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+  const long long H = 3 * m;
+  const long long ntiles = (n + kTwinTile - 1) / kTwinTile;
+  int g = resident_grid(reinterpret_cast<const void*>(k_twin_count), kBlock, 0,
+                        (H + kBlock - 1) / kBlock, &c1);
+  k_twin_count<<<g, kBlock, 0, s>>>(tri, m, n, cnt, C);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  g = resident_grid(reinterpret_cast<const void*>(k_twin_tiles), kBlock, 0, ntiles, &c2);
+  k_twin_tiles<<<g, kBlock, 0, s>>>(cnt, n, tile_sum);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_scan_tiles(tile_sum, tile_off, n, nullptr, n, kTwinTile, &C->scratch0,
+                             &C->scratch1, nullptr, 0, 0, C, s)) != cudaSuccess)
+    return e;
+  g = resident_grid(reinterpret_cast<const void*>(k_twin_start), kBlock, 0, ntiles, &c3);
+  k_twin_start<<<g, kBlock, 0, s>>>(cnt, n, tile_off, start, m);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  g = resident_grid(reinterpret_cast<const void*>(k_twin_fill), kBlock, 0,
+                    (H + kBlock - 1) / kBlock, &c4);
+  k_twin_fill<<<g, kBlock, 0, s>>>(tri, m, n, start, cnt, adj);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  g = resident_grid(reinterpret_cast<const void*>(k_twin_match), kBlock, 0,
+                    (H + kBlock - 1) / kBlock, &c5);
+  (void)sms;
+  k_twin_match<<<g, kBlock, 0, s>>>(tri, m, n, start, adj, twin, C);
+  return cudaGetLastError();
+}
+
+}  // namespace polylla

@@ -282,3 +282,53 @@ def test_lepp(name):
         np.testing.assert_array_equal(r, ref_r)
         np.testing.assert_array_equal(d, ref_d)
         np.testing.assert_array_equal(r2, ref_r)
+
+
+@pytest.mark.parametrize("name", ["golden", "uniform-1k", "uniform-1m", "holes"])
+def test_twin_built_on_device(name):
+    """mesh_create without twin: the twin array built from tri equals the
+    generator's, and the run gives the same polygons."""
+    if name == "golden":
+        meshes = [c["mesh"] for c in golden_cases()] + [grid_mesh(5, 1)[0]]
+    elif name == "holes":
+        meshes = [meshgen.domain_with_holes("gmm", 30_000, 1 << 20, 4)]
+    else:
+        meshes = [meshgen.load(name)]
+    for mesh in meshes:
+        xy = torch.as_tensor(mesh["xy"]).cuda().contiguous()
+        tri = torch.as_tensor(np.ascontiguousarray(mesh["tri"])).cuda().contiguous()
+        h = pg.mesh_create(xy, tri, None, pg.VALIDATE)
+        pg.run(h)
+        off, vtx = (t.cpu().numpy().copy() for t in pg.get_polygons(h))
+        pg.mesh_destroy(h)
+        ref = oracle.run(mesh)
+        np.testing.assert_array_equal(off, ref["off"])
+        np.testing.assert_array_equal(vtx, ref["vtx"])
+
+
+def test_twin_built_on_device_twin_values_and_host_path():
+    mesh = meshgen.load("uniform-1m")
+    n, m = mesh["xy"].shape[0], mesh["tri"].shape[0]
+    hm = pg.mesh_create_host(n, m)
+    xy = torch.from_numpy(mesh["xy"]).reshape(-1).pin_memory()
+    tri = torch.from_numpy(np.ascontiguousarray(mesh["tri"])).reshape(-1).pin_memory()
+    off = torch.empty(m + 1, dtype=torch.int64).pin_memory()
+    vtx = torch.empty(3 * m, dtype=torch.int32).pin_memory()
+    np_, nv = pg.run_host(hm, xy, tri, None, off, vtx)
+    _, _, tw = pg.mesh_inputs(hm, n, m)
+    np.testing.assert_array_equal(tw.cpu().numpy(), mesh["twin"])
+    pg.mesh_destroy(hm)
+    ref = oracle.run(mesh)
+    np.testing.assert_array_equal(off[:np_ + 1].numpy(), ref["off"])
+    np.testing.assert_array_equal(vtx[:nv].numpy(), ref["vtx"])
+
+
+def test_twin_built_on_device_rejects_non_manifold():
+    base = [c["mesh"] for c in golden_cases()][1]
+    tri = np.ascontiguousarray(base["tri"])
+    bad = np.concatenate([tri, tri[:1]])  # a triangle twice: its directed edges twice
+    xy = torch.as_tensor(base["xy"]).cuda().contiguous()
+    t = torch.as_tensor(bad).cuda().contiguous()
+    with pytest.raises(pg.PolyllaError) as e:
+        pg.mesh_create(xy, t, None, 0)
+    assert e.value.code == 3  # POLYLLA_ERR_TOPOLOGY

@@ -104,3 +104,20 @@ def test_served_request_larger_than_budget_fails_cleanly():
     if pg.mesh_footprint(4096 // 2 + 2, 4096, True) + 4096 <= (2 << 20):
         assert r["status"] == 0
     S.close()
+
+
+def test_served_without_twin():
+    """Requests without a twin array: built on the device from tri."""
+    meshes = mixed_meshes(6, 25, 500, 20000)
+    S = pg.Server(budget_bytes=4 << 30, max_slots=4)
+    ids = []
+    for m in meshes:
+        xy, tri, _ = pinned(m)
+        ids.append(S.submit(xy, tri, None))
+    got = drain(S, len(ids))
+    for rid, mesh in zip(ids, meshes):
+        assert got[rid]["status"] == 0
+        off, vtx = plain(mesh)
+        np.testing.assert_array_equal(got[rid]["off"].numpy(), off)
+        np.testing.assert_array_equal(got[rid]["vtx"].numpy(), vtx)
+    S.close()
