@@ -240,6 +240,20 @@ def run_ours(args, dist: Dist) -> dict | None:
     for _ in range(args.kernel_steps):
         M.run(stream)
     recs = pg.kernel_times(M.handle, reset=True)
+    # the twin array from tri on the device (not part of the step): a handle that
+    # builds it, timed per launch
+    tw_h = pg.mesh_create(M.xy, M.tri, None, 0)
+    pg.set_timing(tw_h, True)
+    tw_ms = []
+    for _ in range(5):
+        pg.mesh_build_twin(tw_h, stream)
+        tw_ms += [t for k, t in pg.kernel_times(tw_h, reset=True) if k == "build_twin"]
+    pg.mesh_destroy(tw_h)
+    # the longest-edge paths (not part of the step): mean of a few launches
+    lepp_ms = []
+    for _ in range(5):
+        pg.lepp(M.handle, stream)
+        lepp_ms += [t for k, t in pg.kernel_times(M.handle, reset=True) if k == "lepp"]
     pg.set_timing(M.handle, False)
     per = {}
     for name, ms in recs:
@@ -312,6 +326,27 @@ def run_ours(args, dist: Dist) -> dict | None:
         bad = res is None or res["status"] != 0
         npoly, nvtx = (res["n_poly"], res["n_vtx"]) if not bad else (0, 0)
         e2e_s = dist.max(t1 - t0)
+        # the same, the twin array built on the device from tri (one copy less)
+        S = pg.Server(budget_bytes=int(3.2 * slot), max_slots=3)
+        for k in range(3):
+            S.submit(hxy, htri, None, *outs[k])
+        got = 0
+        while got < 3:
+            got += len(S.poll(wait_us=100000))
+        tn0 = time.perf_counter()
+        free, live = list(range(3)), {}
+        for k in range(args.e2e_steps):
+            while not free:
+                for r in S.poll(wait_us=1000):
+                    free.append(live.pop(r["id"]))
+            b = free.pop()
+            live[S.submit(hxy, htri, None, *outs[b])] = b
+        while live:
+            for r in S.poll(wait_us=1000):
+                free.append(live.pop(r["id"]))
+        tn1 = time.perf_counter()
+        S.close()
+        notwin_s = dist.max(tn1 - tn0)
         # the synchronous entry point, for comparison
         hm = pg.mesh_create_host(n, m)
         pg.run_host(hm, hxy, htri, htwin, outs[0][0], outs[0][1], stream)
@@ -329,7 +364,10 @@ def run_ours(args, dist: Dist) -> dict | None:
                "peak_running": info["peak_running"], "failed": int(bad),
                "sync": {"value": dist.world * m * args.e2e_steps / sync_s,
                         "ms_per_step": 1e3 * sync_s / args.e2e_steps,
-                        "api": "polylla_run_host"}}
+                        "api": "polylla_run_host"},
+               "twin_built_on_device": {"value": dist.world * m * args.e2e_steps / notwin_s,
+                                        "ms_per_step": 1e3 * notwin_s / args.e2e_steps,
+                                        "h2d_bytes_per_step": int(16 * n + 12 * m)}}
 
     M.close()
     out = {
@@ -347,6 +385,11 @@ def run_ours(args, dist: Dist) -> dict | None:
         "label_seed": {"ms": round(ls_ms, 5), "alg_bytes": int(ls_bytes),
                        "gbs": round(ls_bytes / (ls_ms * 1e-3) / 1e9, 1) if ls_ms else None,
                        "frac": round(ls_bytes / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None},
+        "twin_build": {"ms": round(statistics.mean(tw_ms), 5) if tw_ms else None,
+                       "what": "polylla_mesh_build_twin: twin from tri on the device"},
+        "lepp": {"ms": round(statistics.mean(lepp_ms), 5) if lepp_ms else None,
+                 "value": m / (statistics.mean(lepp_ms) * 1e-3) if lepp_ms else None,
+                 "unit": UNIT, "what": "polylla_lepp: region seed and path length per triangle"},
         "step_roofline": {"alg_bytes": int(step_bytes), "gbs": round(step_gbs, 1),
                           "frac": round(step_gbs / peak, 4)},
         "kernels": kernels,
