@@ -37,7 +37,7 @@ struct polylla_mesh {
   bool owns_twin = false;      // twin built on the device (handle-owned)
   int* tw_cnt = nullptr;       // twin construction scratch: per-vertex counts,
   int* tw_start = nullptr;     // first slots (n + 1),
-  int* tw_adj = nullptr;       // outgoing half-edges (3m)
+  int2* tw_adj = nullptr;      // outgoing half-edges with their destinations (3m)
   int phase = kCreated;
   int latest_csr = -1;  // 0: traversal CSR, 1: final CSR
   cudaStream_t last_stream = nullptr;
@@ -153,7 +153,7 @@ void free_all(polylla_mesh* h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_twin && !h->owns_inputs) cudaFree(const_cast<int*>(h->M.twin));
-  for (int* p : {h->tw_cnt, h->tw_start, h->tw_adj})
+  for (void* p : {(void*)h->tw_cnt, (void*)h->tw_start, (void*)h->tw_adj})
     if (p) cudaFree(p);
   if (h->owns_inputs) {
     cudaFree(const_cast<long long*>(h->M.xy));
@@ -849,7 +849,7 @@ polylla_status polylla_get_lepp(polylla_mesh_t h, const int32_t** d_region,
 int64_t polylla_mesh_footprint(int64_t n_vertices, int64_t n_tri, int owns_inputs) {
   if (n_vertices < 3 || n_tri < 1) return -1;
   long long b = derived_bytes(n_vertices, n_tri);
-  if (owns_inputs) b += 16 * n_vertices + 24 * n_tri + 8 * n_vertices + 4 + 12 * n_tri;
+  if (owns_inputs) b += 16 * n_vertices + 24 * n_tri + 8 * n_vertices + 4 + 24 * n_tri;
   return b;
 }
 

@@ -267,9 +267,9 @@ cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const 
                                unsigned long long* status, long long* off, int* vtx,
                                long long* obase, long long m, Counters* C, int grid,
                                cudaStream_t s);
-// The twin array from tri (scratch: cnt n, start n + 1, adj 3m; the tile words).
+// The twin array from tri (scratch: cnt n, start n + 1, adj 3m pairs; the tile words).
 cudaError_t launch_build_twin(const int* tri, long long m, long long n, int* twin, int* cnt,
-                              int* start, int* adj, long long* tile_sum, long long* tile_off,
+                              int* start, int2* adj, long long* tile_sum, long long* tile_off,
                               Counters* C, int sms, cudaStream_t s);
 // Longest-edge propagation paths: per triangle its region's seed and the path length.
 cudaError_t launch_lepp(const DevMesh& M, const uint8_t* lab, int* region, int* depth, Counters* C,

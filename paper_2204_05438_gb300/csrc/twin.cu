@@ -6,9 +6,10 @@
 //   k_twin_count   outgoing half-edges per vertex (atomics), and the per-tile sums
 //                  of those counts for the tile scan;
 //   k_twin_start   each vertex's first slot: its tile's offset + an in-tile scan;
-//   k_twin_fill    every half-edge into its origin's slots;
+//   k_twin_fill    every half-edge, with its destination, into its origin's slots;
 //   k_twin_match   h = u->v finds v->u among v's outgoing half-edges (about six
-//                  on a Delaunay mesh).  A directed edge used twice, or an edge
+//                  on a Delaunay mesh, one or two cache lines of (half-edge,
+//                  destination) pairs).  A directed edge used twice, or an edge
 //                  with more than two triangles, sets POLYLLA_ERR_TOPOLOGY.
 #include "polylla_internal.cuh"
 
@@ -81,19 +82,20 @@ __global__ void __launch_bounds__(kBlock) k_twin_start(int* __restrict__ cnt, lo
 
 __global__ void __launch_bounds__(kBlock) k_twin_fill(const int* __restrict__ tri, long long m,
                                                       long long n, const int* __restrict__ start,
-                                                      int* __restrict__ cnt, int* __restrict__ adj) {
+                                                      int* __restrict__ cnt, int2* __restrict__ adj) {
   const long long H = 3 * m;
   for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
        h += (long long)gridDim.x * blockDim.x) {
     const int v = __ldg(tri + h);
     if (v < 0 || v >= n) continue;
-    adj[start[v] + atomicAdd(cnt + v, 1)] = (int)h;
+    const int w = __ldg(tri + he_next((int)h));
+    adj[start[v] + atomicAdd(cnt + v, 1)] = make_int2((int)h, w);
   }
 }
 
 __global__ void __launch_bounds__(kBlock) k_twin_match(const int* __restrict__ tri, long long m,
                                                        long long n, const int* __restrict__ start,
-                                                       const int* __restrict__ adj,
+                                                       const int2* __restrict__ adj,
                                                        int* __restrict__ twin, Counters* C) {
   const long long H = 3 * m;
   for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
@@ -109,22 +111,22 @@ __global__ void __launch_bounds__(kBlock) k_twin_match(const int* __restrict__ t
     int g = -1, hits = 0;
     const int b0 = start[v], b1 = start[v + 1];
     for (int q = b0; q < b1; ++q) {
-      const int x = adj[q];
-      if (__ldg(tri + he_next(x)) == u) {
-        g = x;
+      const int2 x = adj[q];
+      if (x.y == u) {
+        g = x.x;
         ++hits;
       }
     }
     int same = 0;
     const int a0 = start[u], a1 = start[u + 1];
-    for (int q = a0; q < a1; ++q) same += __ldg(tri + he_next(adj[q])) == v;
+    for (int q = a0; q < a1; ++q) same += adj[q].y == v;
     if (hits > 1 || same != 1) set_error(C, POLYLLA_ERR_TOPOLOGY, 141);
     twin[h] = g;
   }
 }
 
 cudaError_t launch_build_twin(const int* tri, long long m, long long n, int* twin, int* cnt,
-                              int* start, int* adj, long long* tile_sum, long long* tile_off,
+                              int* start, int2* adj, long long* tile_sum, long long* tile_off,
                               Counters* C, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n, s);
   if (e != cudaSuccess) return e;

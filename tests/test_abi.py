@@ -109,4 +109,4 @@ def test_server_argument_errors_need_no_device():
     a = lib.polylla_mesh_footprint(1000, 2000, 0)
     b = lib.polylla_mesh_footprint(1000, 2000, 1)
     # owned inputs: xy, tri, twin and the twin construction's scratch
-    assert 0 < a < b and b - a == 16 * 1000 + 24 * 2000 + 8 * 1000 + 4 + 12 * 2000
+    assert 0 < a < b and b - a == 16 * 1000 + 24 * 2000 + 8 * 1000 + 4 + 24 * 2000
