@@ -133,6 +133,38 @@ def test_disconnected_triangles():
     assert_parity({"xy": xy, "tri": tri, "twin": meshgen.twin_from_tri(tri)})
 
 
+def test_vertex_where_two_fans_touch():
+    # vertex 0 lies in two triangles that share no edge (a bow tie): the
+    # per-vertex successor pass covers one fan, the per-triangle pass the rest
+    xy = np.array([[0, 0], [4, 1], [1, 4], [-4, -1], [-1, -4]], np.int64) + 8
+    tri = np.array([[0, 1, 2], [0, 3, 4]], np.int32)
+    assert_parity({"xy": xy, "tri": tri, "twin": meshgen.twin_from_tri(tri)})
+    # the same inside a larger mesh: carve the triangles around a vertex except two
+    # opposite ones
+    mesh = meshgen.generate("uniform", 2_000, 1 << 20, 31)
+    tri = mesh["tri"]
+    v = int(tri[len(tri) // 2, 0])
+    around = np.nonzero((tri == v).any(axis=1))[0]
+    assert len(around) >= 4
+    keep = np.ones(len(tri), bool)
+    keep[around] = False
+    keep[around[0]] = keep[around[len(around) // 2]] = True
+    tri = np.ascontiguousarray(tri[keep])
+    assert_parity({"xy": mesh["xy"], "tri": tri, "twin": meshgen.twin_fast(tri)})
+
+
+def test_unused_vertices():
+    # vertices no triangle uses: more of them than half-edges, and a few
+    xy = np.concatenate([np.array([[0, 0], [4, 0], [0, 3]], np.int64),
+                         np.arange(20, dtype=np.int64).reshape(10, 2) + 100])
+    tri = np.array([[0, 1, 2]], np.int32)
+    assert_parity({"xy": xy, "tri": tri, "twin": meshgen.twin_from_tri(tri)})
+    mesh = meshgen.generate("gmm", 3_000, 1 << 22, 12)
+    extra = np.array([[(1 << 22) + 5, 7], [(1 << 22) + 9, 11]], np.int64)
+    assert_parity({"xy": np.concatenate([mesh["xy"], extra]), "tri": mesh["tri"],
+                   "twin": mesh["twin"]})
+
+
 def test_uniform_1m_full():
     assert_parity(meshgen.load("uniform-1m"))
 
