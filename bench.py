@@ -276,6 +276,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     label_seed = [k for k in ("label_max", "label_class", "scan_seeds", "seed_write") if k in kernels]
     ls_ms = sum(kernels[k]["ms"] for k in label_seed)
     ls_bytes = sum(kernels[k]["alg_bytes"] for k in label_seed)
+    ls_io = 24 * m + 16 * n + m + 4 * sizes["ns"]
     traffic = None
     if NCU_TRAFFIC["sources"] == source_hash():
         traffic = NCU_TRAFFIC["bytes"].get(dom)
@@ -384,9 +385,15 @@ def run_ours(args, dist: Dist) -> dict | None:
                    "l2": "inputs larger than L2 (640 MB vs 126 MB); no flush",
                    "step": "polylla_run: label + seeds + traverse + repair, inputs resident"},
         "roofline": roofline,
+        # alg_bytes: what the four kernels read and write, each array once (the
+        # Max bytes handed from label_max to label_class and the tf words the
+        # traversal consumes included); alg_bytes_io: the phases' own inputs and
+        # outputs only (tri, xy, twin in; label byte and seed list out)
         "label_seed": {"ms": round(ls_ms, 5), "alg_bytes": int(ls_bytes),
                        "gbs": round(ls_bytes / (ls_ms * 1e-3) / 1e9, 1) if ls_ms else None,
-                       "frac": round(ls_bytes / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None},
+                       "frac": round(ls_bytes / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None,
+                       "alg_bytes_io": int(ls_io),
+                       "frac_io": round(ls_io / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None},
         "twin_build": {"ms": round(statistics.mean(tw_ms), 5) if tw_ms else None,
                        "what": "polylla_mesh_build_twin: twin from tri on the device"},
         "lepp": {"ms": round(statistics.mean(lepp_ms), 5) if lepp_ms else None,
