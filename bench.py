@@ -81,7 +81,7 @@ def hbm_peak():
 def algorithmic_bytes(name: str, s: dict) -> float:
     """Bytes a kernel must move if every element it needs is read or written once
     (n vertices, m triangles, ns seeds, nv0 / nv traversal / final polygon
-    vertices, np final polygons).  The reparation kernels and the long-polygon
+    vertices, np final polygons, ntp polygons with tips).  The reparation kernels and the long-polygon
     kernel touch about 1% of the mesh along dependent-load chains: they are
     latency-bound and carry no byte count."""
     n, m, ns, nv0, nv, npoly = s["n"], s["m"], s["ns"], s["nv0"], s["nv"], s["np"]
@@ -95,8 +95,9 @@ def algorithmic_bytes(name: str, s: dict) -> float:
         # every tf word once, the successor of every frontier half-edge out
         "succ": 12 * m + 4 * nv0,
         # seed and its triangle's tf words, per vertex succ + origin in and pool out,
-        # per polygon its record (start, len, tips, tip, mode, count, length, pos)
-        "walk": 16 * ns + 12 * nv0 + 36 * ns,
+        # per polygon its output record (count, length, pos), and start, length,
+        # tips and tip for each polygon with tips
+        "walk": 16 * ns + 12 * nv0 + 16 * ns + 16 * s.get("ntp", 0),
         # per polygon its piece count and length
         "out_tiles": 8 * ns,
         # per polygon record in, pool in, offsets and vertices out
@@ -261,7 +262,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     for name, ms in recs:
         per.setdefault(name, []).append(ms)
     sizes = {"n": n, "m": m, "ns": st["n_seeds"], "nv0": st["n_vtx_trav"], "nv": st["n_vtx"],
-             "np": st["n_poly"]}
+             "np": st["n_poly"], "ntp": st["n_tip_polygons"]}
     peak, peak_kind = hbm_peak()
     kernels = {}
     step_sum = sum(statistics.mean(v) for v in per.values())
@@ -634,7 +635,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="gmm16-10m")
     ap.add_argument("--kernel-steps", type=int, default=20)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="reference arm: host time of warm-up + steps, which sizes its sample")

@@ -144,7 +144,7 @@ cudaError_t dalloc(T** p, long long count) {
 void free_all(polylla_mesh* h) {
   void* ptrs[] = {h->lab,      h->seeds,     h->succ,      h->tf,
                   h->loc,      h->vstamp,    h->Lg.poly,   h->P.start,    h->P.len,
-                  h->P.ntip,   h->P.mode,    h->P.pcnt,    h->P.pbase,    h->P.flen,
+                  h->P.ntip,   h->P.pcnt,    h->P.pbase,    h->P.flen,
                   h->P.pos,    h->F.pos,     h->F.len,     h->F.h,        h->pool.v,
                   h->tile_sum, h->tile_off,  h->off_trav,  h->vtx_trav,   h->off_final,
                   h->vtx_final, h->C,         h->Dl.poly,   h->P.tip_h,
@@ -219,7 +219,6 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->P.start, m);
   ALLOC(h->P.len, m);
   ALLOC(h->P.ntip, m);
-  ALLOC(h->P.mode, m);
   ALLOC(h->P.pcnt, m);
   ALLOC(h->P.pbase, m);
   ALLOC(h->P.flen, m);
@@ -267,7 +266,6 @@ long long derived_bytes(long long n, long long m) {
   COUNT(c.P.start, m);
   COUNT(c.P.len, m);
   COUNT(c.P.ntip, m);
-  COUNT(c.P.mode, m);
   COUNT(c.P.pcnt, m);
   COUNT(c.P.pbase, m);
   COUNT(c.P.flen, m);

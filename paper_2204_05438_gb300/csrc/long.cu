@@ -26,7 +26,7 @@
 //      decreasing tip order builds that tree) and writes them to the pool.
 //
 // A region too large for the shared-memory budget is handled by one thread of the
-// block with the sequential code (mode 2).
+// block with the sequential code (long_fallback).
 #include "walk.cuh"
 
 namespace polylla {
@@ -153,7 +153,6 @@ __device__ void long_fallback(const DevMesh& M, uint8_t* lab, int* tf, int t0, l
                               PolyArrays& P, FinalPieces& F, Pool& pool, int repair, Counters* C) {
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
-  P.mode[i] = 2;
   P.pcnt[i] = 0;
   P.flen[i] = 0;
   const int e = region_entry_tf(tf, t0, H, limit);
@@ -342,7 +341,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
       continue;
     }
     if (threadIdx.x == 0) {
-      P.mode[i] = 1;
       P.start[i] = mem[c];
       P.len[i] = L;
       P.ntip[i] = nt;

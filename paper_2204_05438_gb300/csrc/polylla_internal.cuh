@@ -208,7 +208,6 @@ struct PolyArrays {
   int* len;       // traversal length
   int* ntip;      // barrier-edge tips
   int* tip_h;     // barrier half-edge ending at the smallest tip vertex, or -1
-  int* mode;      // 0 one thread; 1 one block (long.cu); 2 long, one thread of a block
   int* pcnt;      // output pieces: 0 = the polygon itself, at pos; else records at pbase
   int* pbase;     // first piece record
   int* flen;      // total output length

@@ -163,20 +163,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
     const long long off = warp_alloc(&C->pool_alloc, need);
     if (i >= n) continue;
     if (is_long) {
-      P.mode[i] = 1;
-      P.len[i] = 0;
-      P.ntip[i] = 0;
       P.pcnt[i] = 0;
       P.flen[i] = 0;
       const long long j = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_long), 1ull);
       if (j < Lg.cap) Lg.poly[j] = (int)i;
       continue;
     }
-    P.mode[i] = 0;
-    P.start[i] = start;
-    P.len[i] = closed ? len : 0;
-    P.ntip[i] = closed ? ntips : 0;
-    P.tip_h[i] = tip_h;
+    // start, length and tips are read only by the reparation kernels
     P.pcnt[i] = 0;
     P.flen[i] = 0;
     if (!closed) continue;
@@ -184,6 +177,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
     st_tips += ntips;
     st_tippolys += ntips > 0;
     if (split) {
+      P.start[i] = start;
+      P.len[i] = len;
+      P.ntip[i] = ntips;
+      P.tip_h[i] = tip_h;
       LongList& D = (ntips == 1) ? D1 : Dm;
       long long* cnt = (ntips == 1) ? &C->n_defer : &C->n_multi;
       const long long d = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cnt), 1ull);
