@@ -273,8 +273,9 @@ polylla_status polylla_get_lepp(polylla_mesh_t mesh, const int32_t** d_region,
  * needed).  A schedule sets the longest polygon walked by one thread (longer
  * ones go to one thread block each) and how those blocks are sized (long_mode 0:
  * one large block per polygon; 1: small blocks first, several per SM, handing
- * the regions they cannot hold to large ones); polylla_batch_schedule_info
- * reports both.
+ * the regions they cannot hold to large ones) and whether the three kernels after
+ * the walk overlap on side streams (overlap 1) or run one after another (0);
+ * polylla_batch_schedule_info reports all three.
  *
  * polylla_batch_tune times every schedule on this batch (`reps` graph replays
  * each, after one warm-up), stores the fastest, and returns it in *best and the
@@ -298,7 +299,8 @@ polylla_status polylla_batch_create(const int64_t* d_xy, const int64_t* d_vtx_of
                                     const int64_t* d_tri_off, int64_t n_meshes, uint32_t flags,
                                     void* stream, polylla_batch_t* out);
 int polylla_batch_schedules(void);
-polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_mode);
+polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_mode,
+                                           int* overlap);
 polylla_status polylla_batch_tune(polylla_batch_t batch, int reps, void* stream, int* best,
                                   float* ms);
 polylla_status polylla_batch_run(polylla_batch_t batch, int schedule, void* stream);

@@ -106,7 +106,8 @@ def load_library(path: str | None = None):
             "polylla_label_seeds_noalloc": ([vp, i64, vp, vp, i64, vp, vp, vp, vp], st),
             "polylla_batch_create": ([vp, vp, vp, vp, vp, i64, u32, vp, ctypes.POINTER(vp)], st),
             "polylla_batch_schedules": ([], i32),
-            "polylla_batch_schedule_info": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+            "polylla_batch_schedule_info": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                             ctypes.POINTER(i32)], st),
             "polylla_batch_tune": ([vp, i32, vp, ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float)], st),
             "polylla_batch_run": ([vp, i32, vp], st),
@@ -346,11 +347,11 @@ def batch_schedules() -> int:
 
 
 def batch_schedule_info(schedule: int) -> dict:
-    cap, thr = ctypes.c_int(), ctypes.c_int()
+    cap, thr, ovl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load_library().polylla_batch_schedule_info(schedule, ctypes.byref(cap),
-                                                      ctypes.byref(thr)),
+                                                      ctypes.byref(thr), ctypes.byref(ovl)),
            "polylla_batch_schedule_info")
-    return {"walk_cap": cap.value, "long_mode": thr.value}
+    return {"walk_cap": cap.value, "long_mode": thr.value, "overlap": ovl.value}
 
 
 def batch_tune(batch: int, reps: int = 3, stream=None):

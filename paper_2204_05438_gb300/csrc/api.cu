@@ -74,6 +74,7 @@ struct polylla_mesh {
 
   // schedule: the walk's thread-per-seed cap and the long-polygon mode
   int walk_cap = kWalkCap;
+  bool overlap = true;  // the kernels after the walk on side streams
   int long_mode = 0;
   bool lepp_valid = false;
   long long* obase = nullptr;  // batches: output index of each traversal polygon
@@ -357,7 +358,7 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
                        h->walk_cap, repair, h->C, gw, s);
   }));
   // repair_one (this stream), repair_multi and long (side streams) at once
-  const bool fork = !h->timing;
+  const bool fork = !h->timing && h->overlap;
   cudaStream_t s1 = s, s2 = s;
   if (fork) {
     POLY_TRY(cuda_status(cudaEventRecord(h->fork, s)));
@@ -457,11 +458,14 @@ polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags) {
 }
 
 // ---------------------------------------------------------------- batches
-// Schedules a batch can be run with: the walk's thread-per-seed cap, and the
-// long-polygon mode (0: large blocks only; 1: small blocks first).
-constexpr int kSchedules = 4;
-constexpr int kSchedCap[kSchedules] = {64, 64, 32, 48};
-constexpr int kSchedLong[kSchedules] = {0, 1, 1, 1};
+// Schedules a batch can be run with: the walk's thread-per-seed cap, the
+// long-polygon mode (0: large blocks only; 1: small blocks first), and whether
+// the three kernels after the walk overlap on side streams (1) or run one after
+// another (0: each one-wave grid then has the whole GPU to itself).
+constexpr int kSchedules = 8;
+constexpr int kSchedCap[kSchedules] = {64, 64, 32, 48, 64, 64, 32, 48};
+constexpr int kSchedLong[kSchedules] = {0, 1, 1, 1, 0, 1, 1, 1};
+constexpr int kSchedOverlap[kSchedules] = {1, 1, 1, 1, 0, 0, 0, 0};
 
 }  // namespace
 
@@ -521,6 +525,7 @@ polylla_status batch_run_sched(polylla_batch* b, int k, cudaStream_t s) {
   polylla_mesh* h = b->mesh;
   h->walk_cap = kSchedCap[k];
   h->long_mode = kSchedLong[k];
+  h->overlap = kSchedOverlap[k] != 0;
   b->pfirst_valid = false;
   if (h->timing) return batch_body(b, s);
   if (!b->exec[k]) {
@@ -978,10 +983,12 @@ polylla_status polylla_batch_create(const int64_t* d_xy, const int64_t* d_vtx_of
 
 int polylla_batch_schedules(void) { return kSchedules; }
 
-polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_mode) {
+polylla_status polylla_batch_schedule_info(int schedule, int* walk_cap, int* long_mode,
+                                           int* overlap) {
   if (schedule < 0 || schedule >= kSchedules) return POLYLLA_ERR_INVALID_ARG;
   if (walk_cap) *walk_cap = kSchedCap[schedule];
   if (long_mode) *long_mode = kSchedLong[schedule];
+  if (overlap) *overlap = kSchedOverlap[schedule];
   return POLYLLA_OK;
 }
 

@@ -85,12 +85,13 @@ def test_batch_argument_errors_need_no_device():
     assert lib.polylla_batch_destroy(None) == 1
     k = lib.polylla_batch_schedules()
     assert k >= 2
-    cap, thr = ctypes.c_int(), ctypes.c_int()
+    cap, thr, ovl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     for s in range(k):
-        assert lib.polylla_batch_schedule_info(s, ctypes.byref(cap), ctypes.byref(thr)) == 0
-        assert cap.value in (16, 32, 48, 64) and thr.value in (0, 1)
-    assert lib.polylla_batch_schedule_info(k, ctypes.byref(cap), ctypes.byref(thr)) == 1
-    assert lib.polylla_batch_schedule_info(-1, None, None) == 1
+        assert lib.polylla_batch_schedule_info(s, ctypes.byref(cap), ctypes.byref(thr),
+                                               ctypes.byref(ovl)) == 0
+        assert cap.value in (16, 32, 48, 64) and thr.value in (0, 1) and ovl.value in (0, 1)
+    assert lib.polylla_batch_schedule_info(k, ctypes.byref(cap), ctypes.byref(thr), None) == 1
+    assert lib.polylla_batch_schedule_info(-1, None, None, None) == 1
 
 
 def test_server_argument_errors_need_no_device():
