@@ -273,7 +273,8 @@ polylla_status polylla_get_lepp(polylla_mesh_t mesh, const int32_t** d_region,
  * needed).  A schedule sets the longest polygon walked by one thread (longer
  * ones go to one thread block each) and how those blocks are sized (long_mode 0:
  * one large block per polygon; 1: small blocks first, several per SM, handing
- * the regions they cannot hold to large ones) and whether the three kernels after
+ * the regions they cannot hold to large ones; 2: the same with one warp per
+ * polygon first) and whether the three kernels after
  * the walk overlap on side streams (overlap 1) or run one after another (0);
  * polylla_batch_schedule_info reports all three.
  *

@@ -459,13 +459,14 @@ polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags) {
 
 // ---------------------------------------------------------------- batches
 // Schedules a batch can be run with: the walk's thread-per-seed cap, the
-// long-polygon mode (0: large blocks only; 1: small blocks first), and whether
-// the three kernels after the walk overlap on side streams (1) or run one after
-// another (0: each one-wave grid then has the whole GPU to itself).
-constexpr int kSchedules = 8;
-constexpr int kSchedCap[kSchedules] = {64, 64, 32, 48, 64, 64, 32, 48};
-constexpr int kSchedLong[kSchedules] = {0, 1, 1, 1, 0, 1, 1, 1};
-constexpr int kSchedOverlap[kSchedules] = {1, 1, 1, 1, 0, 0, 0, 0};
+// long-polygon mode (0: large blocks only; 1: small blocks first; 2: one warp per
+// polygon first), and whether the three kernels after the walk overlap on side
+// streams (1) or run one after another (0: each one-wave grid then has the whole
+// GPU to itself).
+constexpr int kSchedules = 12;
+constexpr int kSchedCap[kSchedules] = {64, 64, 32, 48, 64, 64, 32, 48, 16, 32, 16, 32};
+constexpr int kSchedLong[kSchedules] = {0, 1, 1, 1, 0, 1, 1, 1, 2, 2, 2, 2};
+constexpr int kSchedOverlap[kSchedules] = {1, 1, 1, 1, 0, 0, 0, 0, 1, 1, 0, 0};
 
 }  // namespace
 

@@ -41,6 +41,8 @@ constexpr int kLT = 4096;  // BFS queue: triangles of one long region
 constexpr int kSmallThreads = 128;
 constexpr int kSmallLM = 512;
 constexpr int kSmallLT = 512;
+constexpr int kWarpLM = 128;  // one warp per polygon: up to 128 members and triangles
+constexpr int kWarpLT = 128;
 
 template <int LM, int LT>
 constexpr int long_smem_ints() { return LT + 10 * LM; }
@@ -670,10 +672,15 @@ cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seed
     return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg,
                                                  &C->n_long, none, nullptr, loc, vstamp, epoch,
                                                  repair, C, sms, s);
-  // small blocks first; the regions they cannot hold, in large blocks
-  cudaError_t e = launch_long_t<kSmallThreads, kSmallLM, kSmallLT>(
-      M, lab, tf, seeds, succ, P, F, pool, Lg, &C->n_long, Lg2, &C->n_long2, loc, vstamp, epoch,
-      repair, C, 16 * sms, s);
+  // small blocks (mode 1) or one warp per polygon (mode 2) first; the regions
+  // they cannot hold, in large blocks
+  cudaError_t e =
+      mode == 2 ? launch_long_t<32, kWarpLM, kWarpLT>(M, lab, tf, seeds, succ, P, F, pool, Lg,
+                                                      &C->n_long, Lg2, &C->n_long2, loc, vstamp,
+                                                      epoch, repair, C, 32 * sms, s)
+                : launch_long_t<kSmallThreads, kSmallLM, kSmallLT>(
+                      M, lab, tf, seeds, succ, P, F, pool, Lg, &C->n_long, Lg2, &C->n_long2, loc,
+                      vstamp, epoch, repair, C, 16 * sms, s);
   if (e != cudaSuccess) return e;
   return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg2,
                                                &C->n_long2, none, nullptr, loc, vstamp, epoch,

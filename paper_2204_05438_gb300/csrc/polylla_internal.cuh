@@ -254,7 +254,8 @@ cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const i
                                 const LongList& Dm, Counters* C, int sms, cudaStream_t s);
 // One block per long polygon: gather, rank and, if `repair`, split.  mode 0:
 // large blocks only; mode 1: small blocks first, the regions they cannot hold
-// (listed in Lg2) then in large blocks.
+// (listed in Lg2) then in large blocks; mode 2: the same with one-warp blocks
+// first.
 cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seeds, const int* succ,
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                         const LongList& Lg, const LongList& Lg2, int* loc, int* vstamp, int epoch,

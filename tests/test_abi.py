@@ -89,7 +89,7 @@ def test_batch_argument_errors_need_no_device():
     for s in range(k):
         assert lib.polylla_batch_schedule_info(s, ctypes.byref(cap), ctypes.byref(thr),
                                                ctypes.byref(ovl)) == 0
-        assert cap.value in (16, 32, 48, 64) and thr.value in (0, 1) and ovl.value in (0, 1)
+        assert cap.value in (16, 32, 48, 64) and thr.value in (0, 1, 2) and ovl.value in (0, 1)
     assert lib.polylla_batch_schedule_info(k, ctypes.byref(cap), ctypes.byref(thr), None) == 1
     assert lib.polylla_batch_schedule_info(-1, None, None, None) == 1
 
