@@ -350,7 +350,9 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   POLY_TRY(cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(h->C) + first, 0, last - first, s)));
   if (repair == 0 || h->phase < kTraversed) {
     const int gt = grid_for(h, M.m, kBlock);
-    POLY_TRY(launch(h, "succ", s, [&] { return launch_succ(M, h->tf, h->succ, h->C, gt, s); }));
+    POLY_TRY(launch(h, "succ", s, [&] {
+      return launch_succ(M, h->lab, h->tf, h->succ, h->C, gt, s);
+    }));
   }
   const int gw = grid_for(h, M.m, 4 * 256);
   POLY_TRY(launch(h, "walk", s, [&] {

@@ -237,8 +237,9 @@ struct LongList {
   long long cap;
 };
 
-cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
-                        cudaStream_t s);
+// lab: the label bytes (their frontier bits select the half-edges to turn)
+cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
+                        Counters* C, int grid, cudaStream_t s);
 // One thread per seed: walk (<= kWalkCap) and, if `repair`, split the polygon.
 // cap: polygons longer than cap (16, 32, 48 or 64) go to the long-polygon blocks.
 cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,

@@ -1,10 +1,10 @@
 // Traversal (Section 3.2.2, Algorithms 3 and 4) and, for ordinary polygons,
 // reparation (Section 3.2.3, Algorithm 5) in one pass.
 //
-//   k_succ  one thread per triangle: for each frontier half-edge, the next
-//           frontier half-edge of its region's boundary (PolyConstruction's
-//           turn), with the barrier-edge tip flag.  The three turns of a triangle
-//           advance together so their loads overlap.
+//   k_succ  for each frontier half-edge, the next frontier half-edge of its
+//           region's boundary (PolyConstruction's turn), with the barrier-edge
+//           tip flag; each warp compacts the frontier half-edges of 256
+//           triangles and turns them one per lane.
 //   k_walk  one thread per seed: enter the region (at the entry half-edge the
 //           seed kernel found), chase succ around the cycle (at most kWalkCap
 //           vertices, staged in shared memory), note the canonical start and the
@@ -26,58 +26,100 @@
 
 namespace polylla {
 
-__global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const int* __restrict__ tf,
+// Each warp takes 256 consecutive triangles at a time: their frontier half-edges
+// (label bits 2-4, 8 triangles per lane) are compacted into the warp's list in
+// shared memory by a warp scan, in increasing order, and then turned 32 at a
+// time, one per lane: no lane idles on a half-edge that is not frontier, and the
+// 32 turns of a round start at neighbouring half-edges.
+constexpr int kSuccChunk = 256;  // triangles per warp and round of compaction
+constexpr int kSuccPer = kSuccChunk / 32;
+
+__global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const uint8_t* __restrict__ lab,
+                                                 const int* __restrict__ tf,
                                                  int* __restrict__ succ, Counters* C) {
+  // half-edge offsets inside the chunk (< 3 * kSuccChunk): 16 bits leave the L1
+  // the turns read from
+  __shared__ unsigned short s_list[kBlock / 32][3 * kSuccChunk];
   const long long m = M.m;
   const int H = (int)(3 * m);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
-       t += (long long)gridDim.x * blockDim.x) {
-    int x[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) x[k] = __ldg(tf + 3 * t + k);
-    int cur[3], y[3];
-    unsigned active = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      cur[k] = 0;
-      y[k] = 0;
-      if (x[k] >= 0) continue;  // not frontier: no successor
-      const int kn = (k == 2) ? 0 : k + 1;
-      cur[k] = (int)(3 * t + kn);
-      y[k] = x[kn];
-      active |= 1u << k;
-    }
-    for (long long step = 0; active && step <= 3 * m; ++step) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (!((active >> k) & 1u)) continue;
-        if (y[k] < 0) {  // reached a frontier half-edge
-          const int g = cur[k];
-          succ[3 * t + k] = (g == tf_twin(x[k])) ? (g | kTipFlag) : g;
-          active &= ~(1u << k);
-          continue;
-        }
-        if (y[k] >= H) {
-          set_error(C, POLYLLA_ERR_LIMIT, 50);
-          succ[3 * t + k] = (int)(3 * t + k);
-          active &= ~(1u << k);
-          continue;
-        }
-        cur[k] = he_next(y[k]);
+  const int lane = threadIdx.x & 31;
+  unsigned short* list = s_list[threadIdx.x >> 5];
+  const long long nchunks = (m + kSuccChunk - 1) / kSuccChunk;
+  const bool aligned8 = (reinterpret_cast<uintptr_t>(lab) & 7u) == 0;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  // the label bytes of this lane's 8 triangles of chunk ch (loaded one chunk ahead)
+  auto load8 = [&](long long ch, unsigned& lo, unsigned& hi) {
+    lo = 0;
+    hi = 0;
+    if (ch >= nchunks) return;
+    const long long t0 = ch * kSuccChunk + (long long)lane * kSuccPer;
+    if (t0 + kSuccPer <= m && aligned8) {
+      const uint2 v = __ldg(reinterpret_cast<const uint2*>(lab + t0));
+      lo = v.x;
+      hi = v.y;
+    } else {
+      for (int i = 0; i < kSuccPer && t0 + i < m; ++i) {
+        const unsigned b = __ldg(lab + t0 + i);
+        if (i < 4) lo |= b << (8 * i);
+        else hi |= b << (8 * (i - 4));
       }
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if ((active >> k) & 1u) y[k] = tf[cur[k]];
     }
-    if (active) set_error(C, POLYLLA_ERR_LIMIT, 50);
+  };
+  long long ch = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  unsigned nlo, nhi;
+  load8(ch, nlo, nhi);
+  for (; ch < nchunks; ch += nwarps) {
+    const unsigned lo = nlo, hi = nhi;
+    load8(ch + nwarps, nlo, nhi);
+    // bit 3i + k: half-edge k of the lane's triangle i is frontier
+    unsigned mask = 0;
+#pragma unroll
+    for (int i = 0; i < kSuccPer; ++i) {
+      const unsigned b = (i < 4 ? lo >> (8 * i) : hi >> (8 * (i - 4))) & 0xffu;
+      mask |= ((b >> 2) & 7u) << (3 * i);
+    }
+    const int c = __popc(mask);
+    int incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = incl - c;
+    const int o0 = 3 * kSuccPer * lane;  // this lane's first half-edge in the chunk
+    while (mask) {
+      const int s = __ffs(mask) - 1;
+      mask &= mask - 1;
+      list[pos++] = (unsigned short)(o0 + s);
+    }
+    __syncwarp();
+    const int hc = (int)(3 * ch * kSuccChunk);  // the chunk's first half-edge
+    for (int j = lane; j < total; j += 32) {
+      const int h = hc + list[j];
+      const int x = __ldg(tf + h);
+      int cur = he_next(h);
+      int y = __ldg(tf + cur);
+      for (int steps = 0; y >= 0;) {
+        if (y >= H || ++steps > H) {
+          set_error(C, POLYLLA_ERR_LIMIT, 50);
+          cur = h;
+          break;
+        }
+        cur = he_next(y);
+        y = __ldg(tf + cur);
+      }
+      succ[h] = (cur == tf_twin(x)) ? (cur | kTipFlag) : cur;
+    }
+    __syncwarp();
   }
 }
 
-cudaError_t launch_succ(const DevMesh& M, const int* tf, int* succ, Counters* C, int grid,
-                        cudaStream_t s) {
+cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
+                        Counters* C, int grid, cudaStream_t s) {
   static int cap = 0;
   grid = resident_grid(reinterpret_cast<const void*>(k_succ), kBlock, 0, grid, &cap);
-  k_succ<<<grid, kBlock, 0, s>>>(M, tf, succ, C);
+  k_succ<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, C);
   return cudaGetLastError();
 }
 
