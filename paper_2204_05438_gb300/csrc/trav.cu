@@ -148,8 +148,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
                                                        Pool pool, LongList Lg, LongList D1,
                                                        LongList Dm, int cap, int repair,
                                                        Counters* C) {
+  // staging transposed (word q of thread x at q * blockDim + x): the lanes of a
+  // warp, writing the same position in lockstep, hit 32 different banks
   extern __shared__ int sbuf[];
-  int* my = sbuf + threadIdx.x * cap;
+  int* my = sbuf + threadIdx.x;
   const long long n = C->n_seeds;
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
         bool ok = true;
         do {
           const int o = M.tri[h];
-          my[len] = o;
+          my[len * kWalkThreads] = o;
           const unsigned long long key = ((unsigned long long)(unsigned)o << 32) | (unsigned)h;
           if (key < best) {
             best = key;
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
       int* out = pool.v + off;
       int r = rank0;
       for (int q = 0; q < len; ++q) {
-        out[q] = my[r];
+        out[q] = my[r * kWalkThreads];
         if (++r == len) r = 0;
       }
       P.pos[i] = off;
