@@ -63,7 +63,7 @@ cudaError_t launch_batch_globalize(const int* tri, const int* twin, const long l
                                    const long long* vtx_off, long long n_meshes, long long m,
                                    int* tri_g, int* twin_g, Counters* C, int grid,
                                    cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_batch_globalize), kBlock, 0, grid, &cap);
   k_batch_globalize<<<grid, kBlock, 0, s>>>(tri, twin, tri_off, vtx_off, n_meshes, m, tri_g,
                                             twin_g, C);

@@ -181,7 +181,7 @@ cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const 
                                unsigned long long* status, long long* off, int* vtx,
                                long long* obase, long long m, Counters* C, int grid,
                                cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_final_write), kBlock, 0, grid, &cap);
   k_final_write<<<grid, kBlock, 0, s>>>(P, F, pool, status, off, vtx, obase, m, C);
   return cudaGetLastError();

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_label_max(DevMesh M, uint8_t* __r
 
 cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int grid,
                              cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_label_max), kBlock, 0, grid, &cap);
   k_label_max<<<grid, kBlock, 0, s>>>(M, lab, C);
   return cudaGetLastError();
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* l
 
 cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, int* tf,
                                Counters* C, int grid, cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_label_class), kBlock, 0, grid, &cap);
   k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tile_sum, tf, C);
   return cudaGetLastError();
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
 
 cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
                               int* seeds, int* entry, int grid, cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_seed_write), kBlock, 0, grid, &cap);
   k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, tile_off, seeds, entry);
   return cudaGetLastError();

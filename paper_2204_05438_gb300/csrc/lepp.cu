@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kBlock) k_lepp(DevMesh M, const uint8_t* __res
 
 cudaError_t launch_lepp(const DevMesh& M, const uint8_t* lab, int* region, int* depth, Counters* C,
                         int grid, cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_lepp), kBlock, 0, grid, &cap);
   k_lepp<<<grid, kBlock, 0, s>>>(M, lab, region, depth, C);
   return cudaGetLastError();

@@ -7,6 +7,7 @@
 // (bits 0-1), the frontier flag of each edge (bits 2-4), the Seed array (bit 5)
 // and "the longest edge is terminal" (bit 6).
 #pragma once
+#include <atomic>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -167,9 +168,12 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 // SMs at once (from the occupancy calculator, cached per kernel in *cache),
 // and no more than `want` blocks.  A second, partial wave would leave its blocks
 // with as many iterations as the first wave's, after it.
+// cache: one per launcher (a function-local static), written once with the same
+// value by whichever thread launches first
 inline int resident_grid(const void* kernel, int threads, size_t smem, long long want,
-                         int* cache) {
-  if (*cache <= 0) {
+                         std::atomic<int>* cache) {
+  int cached = cache->load(std::memory_order_relaxed);
+  if (cached <= 0) {
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
             cudaSuccess ||
@@ -179,9 +183,10 @@ inline int resident_grid(const void* kernel, int threads, size_t smem, long long
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         sms < 1)
       sms = 1;
-    *cache = per_sm * sms;
+    cached = per_sm * sms;
+    cache->store(cached, std::memory_order_relaxed);
   }
-  long long g = want < *cache ? want : *cache;
+  long long g = want < cached ? want : cached;
   return (int)(g < 1 ? 1 : g);
 }
 

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const uint8_t* __res
 
 cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
                         Counters* C, int grid, cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_succ), kBlock, 0, grid, &cap);
   k_succ<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, C);
   return cudaGetLastError();
@@ -264,13 +264,13 @@ cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* 
                         Counters* C, int grid, cudaStream_t s) {
   if (cap < 16 || cap > kWalkCap || cap % 16) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int) * (size_t)kWalkThreads * cap;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {
     cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(int) * kWalkThreads * kWalkCap));
     attr = true;
   }
-  static int resident[kWalkCap / 16 + 1] = {};
+  static std::atomic<int> resident[kWalkCap / 16 + 1] = {};
   grid = resident_grid(reinterpret_cast<const void*>(k_walk), kWalkThreads, smem, grid,
                        &resident[cap / 16]);
   k_walk<<<grid, kWalkThreads, smem, s>>>(M, tf, entry, succ, P, pool, Lg, D1, Dm, cap, repair,
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                               const LongList& D1, Counters* C, int sms, cudaStream_t s) {
-  static int cap = 0;
+  static std::atomic<int> cap{0};
   const int grid = resident_grid(reinterpret_cast<const void*>(k_repair_one), kBlock, 0,
                                  (long long)sms * 8, &cap);
   k_repair_one<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, P, F, pool, D1, C);
@@ -616,8 +616,8 @@ cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int
 cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                                 const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                                 const LongList& Dm, Counters* C, int sms, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {
     cudaFuncSetAttribute(k_repair_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kRsSmem);
     attr = true;

@@ -130,7 +130,7 @@ cudaError_t launch_build_twin(const int* tri, long long m, long long n, int* twi
                               Counters* C, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n, s);
   if (e != cudaSuccess) return e;
-  static int c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+  static std::atomic<int> c1{0}, c2{0}, c3{0}, c4{0}, c5{0};
   const long long H = 3 * m;
   const long long ntiles = (n + kTwinTile - 1) / kTwinTile;
   int g = resident_grid(reinterpret_cast<const void*>(k_twin_count), kBlock, 0,
