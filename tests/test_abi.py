@@ -65,6 +65,19 @@ def test_argument_errors_need_no_device():
     assert lib.polylla_launch_count(None) == -1
 
 
+def test_size_limits_need_no_device():
+    # 3 <= n < 2^30 vertices and 1 <= m < 2^29 triangles: an empty mesh and one past
+    # either limit are argument errors before any CUDA call (16 stands in for an
+    # aligned device pointer; it is never dereferenced)
+    lib = pg.load_library()
+    h = ctypes.c_void_p(123)
+    for n, m in [(3, 0), (3, -1), (2, 1), ((1 << 30), 1), (3, (1 << 29))]:
+        assert lib.polylla_mesh_create(16, n, 16, m, 16, 0, None, ctypes.byref(h)) == 1, (n, m)
+        assert h.value is None
+        assert lib.polylla_mesh_create_host(n, m, ctypes.byref(h)) == 1, (n, m)
+    assert lib.polylla_mesh_footprint((1 << 30) - 1, (1 << 29) - 1, 1) > 0
+
+
 def test_compiled_for_sm103a_only():
     flags = pbuild.compile_flags()
     assert "arch=compute_103a,code=sm_103a" in flags
