@@ -285,11 +285,10 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
     } else {
       for (int j = 0; j < kPer && t0 + j < m; ++j) w[j >> 2] |= (unsigned)__ldg(lab + t0 + j) << (8 * (j & 3));
     }
-    int cnt = 0;
+    unsigned smask = 0;  // bit i: triangle t0 + i is a seed
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) cnt += (w[q] >> (8 * j + 5)) & 1;
+    for (int i = 0; i < kPer; ++i) smask |= ((w[i >> 2] >> (8 * (i & 3) + 5)) & 1u) << i;
+    const int cnt = __popc(smask);
     int incl = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -305,19 +304,15 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
       total += sw[v];
     }
     int pos = before + incl - cnt;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const unsigned b = w[q] >> (8 * j);
-        if ((b >> 5) & 1u) {
-          const int t = (int)(t0 + 4 * q + j);
-          const unsigned fr = (b >> 2) & 7u;
-          s_seed[pos] = t;
-          s_entry[pos] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
-          ++pos;
-        }
-      }
+    while (smask) {  // the seeds only, in increasing order
+      const int i = __ffs(smask) - 1;
+      smask &= smask - 1;
+      const unsigned wq = i < 8 ? (i < 4 ? w[0] : w[1]) : (i < 12 ? w[2] : w[3]);
+      const unsigned fr = (wq >> (8 * (i & 3) + 2)) & 7u;
+      const int t = (int)(t0 + i);
+      s_seed[pos] = t;
+      s_entry[pos] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
+      ++pos;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < total; k += kBlock) {
