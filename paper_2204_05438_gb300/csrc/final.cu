@@ -32,7 +32,7 @@ __device__ __forceinline__ void out_counts(const PolyArrays& P, long long i, lon
 constexpr int kSub = 4;
 constexpr int kOutTile = kSub * kPolyTile;
 
-__global__ void __launch_bounds__(kBlock, 4) k_final_write(PolyArrays P, FinalPieces F, Pool pool,
+__global__ void __launch_bounds__(kBlock, 5) k_final_write(PolyArrays P, FinalPieces F, Pool pool,
                                                         unsigned long long* status,
                                                         long long* __restrict__ off,
                                                         int* __restrict__ vtx,
