@@ -10,25 +10,34 @@
 //   k_twin_match   h = u->v finds v->u among v's outgoing half-edges (about six
 //                  on a Delaunay mesh, one or two cache lines of (half-edge,
 //                  destination) pairs).  A directed edge used twice, or an edge
-//                  with more than two triangles, sets POLYLLA_ERR_TOPOLOGY.
+//                  with more than two triangles, sets POLYLLA_ERR_TOPOLOGY: an
+//                  edge with more than two triangles repeats a directed edge,
+//                  and a repeated u->v is two hits for the thread of a v->u, or,
+//                  with no v->u, two entries in u's list.
 #include "polylla_internal.cuh"
 
 namespace polylla {
 
 constexpr int kTwinTile = kTriTile;  // vertices per tile of the count scan
 
+// Lanes of a warp holding the same vertex add to its count with one atomic (the
+// half-edges of neighbouring triangles share vertices).  The loop bound is
+// rounded up to whole warps so that every lane takes part in the match.
 __global__ void __launch_bounds__(kBlock) k_twin_count(const int* __restrict__ tri, long long m,
                                                        long long n, int* __restrict__ cnt,
                                                        Counters* C) {
   const long long H = 3 * m;
-  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
+  const long long Hw = (H + 31) / 32 * 32;
+  const int lane = threadIdx.x & 31;
+  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < Hw;
        h += (long long)gridDim.x * blockDim.x) {
-    const int v = __ldg(tri + h);
-    if (v < 0 || v >= n) {
+    int v = h < H ? __ldg(tri + h) : -1;
+    if (h < H && (v < 0 || v >= n)) {
       set_error(C, POLYLLA_ERR_RANGE, 140);
-      continue;
+      v = -1;
     }
-    atomicAdd(cnt + v, 1);
+    const unsigned same = __match_any_sync(0xffffffffu, v);
+    if (v >= 0 && lane == __ffs(same) - 1) atomicAdd(cnt + v, __popc(same));
   }
 }
 
@@ -80,22 +89,37 @@ __global__ void __launch_bounds__(kBlock) k_twin_start(int* __restrict__ cnt, lo
   if (blockIdx.x == 0 && threadIdx.x == 0) start[n] = (int)(3 * m);
 }
 
+// Each origin's slots: the half-edges' destinations in adj_dst, the half-edges
+// themselves at the same positions in adj_he.  Lanes with the same origin take
+// consecutive slots from one atomic.
 __global__ void __launch_bounds__(kBlock) k_twin_fill(const int* __restrict__ tri, long long m,
                                                       long long n, const int* __restrict__ start,
-                                                      int* __restrict__ cnt, int2* __restrict__ adj) {
+                                                      int* __restrict__ cnt,
+                                                      int* __restrict__ adj_dst,
+                                                      int* __restrict__ adj_he) {
   const long long H = 3 * m;
-  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
+  const long long Hw = (H + 31) / 32 * 32;
+  const int lane = threadIdx.x & 31;
+  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < Hw;
        h += (long long)gridDim.x * blockDim.x) {
-    const int v = __ldg(tri + h);
-    if (v < 0 || v >= n) continue;
-    const int w = __ldg(tri + he_next((int)h));
-    adj[start[v] + atomicAdd(cnt + v, 1)] = make_int2((int)h, w);
+    int v = h < H ? __ldg(tri + h) : -1;
+    if (v >= n) v = -1;
+    const unsigned same = __match_any_sync(0xffffffffu, v);
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (v >= 0 && lane == leader) base = atomicAdd(cnt + v, __popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (v < 0) continue;
+    const int q = start[v] + base + __popc(same & ((1u << lane) - 1u));
+    adj_dst[q] = __ldg(tri + he_next((int)h));
+    adj_he[q] = (int)h;
   }
 }
 
 __global__ void __launch_bounds__(kBlock) k_twin_match(const int* __restrict__ tri, long long m,
                                                        long long n, const int* __restrict__ start,
-                                                       const int2* __restrict__ adj,
+                                                       const int* __restrict__ adj_dst,
+                                                       const int* __restrict__ adj_he,
                                                        int* __restrict__ twin, Counters* C) {
   const long long H = 3 * m;
   for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
@@ -106,20 +130,25 @@ __global__ void __launch_bounds__(kBlock) k_twin_match(const int* __restrict__ t
       twin[h] = -1;
       continue;
     }
-    // the twin: v -> u among v's outgoing half-edges; a second v -> u, or a second
-    // u -> v among u's, is a non-manifold edge
+    // the twin: v -> u among v's outgoing half-edges.  A second v -> u is a
+    // non-manifold edge.  A second u -> v shows up as two hits in the scan of
+    // u's list made for a v -> u, when there is one; so u's own list is scanned
+    // only when h has no twin
     int g = -1, hits = 0;
     const int b0 = start[v], b1 = start[v + 1];
     for (int q = b0; q < b1; ++q) {
-      const int2 x = adj[q];
-      if (x.y == u) {
-        g = x.x;
+      if (__ldg(adj_dst + q) == u) {
+        g = q;
         ++hits;
       }
     }
-    int same = 0;
-    const int a0 = start[u], a1 = start[u + 1];
-    for (int q = a0; q < a1; ++q) same += adj[q].y == v;
+    if (hits) g = __ldg(adj_he + g);
+    int same = 1;
+    if (hits == 0) {
+      same = 0;
+      const int a0 = start[u], a1 = start[u + 1];
+      for (int q = a0; q < a1; ++q) same += __ldg(adj_dst + q) == v;
+    }
     if (hits > 1 || same != 1) set_error(C, POLYLLA_ERR_TOPOLOGY, 141);
     twin[h] = g;
   }
@@ -146,14 +175,17 @@ cudaError_t launch_build_twin(const int* tri, long long m, long long n, int* twi
   g = resident_grid(reinterpret_cast<const void*>(k_twin_start), kBlock, 0, ntiles, &c3);
   k_twin_start<<<g, kBlock, 0, s>>>(cnt, n, tile_off, start, m);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the pair buffer (3m int2) as two int arrays of 3m
+  int* adj_dst = reinterpret_cast<int*>(adj);
+  int* adj_he = adj_dst + H;
   g = resident_grid(reinterpret_cast<const void*>(k_twin_fill), kBlock, 0,
                     (H + kBlock - 1) / kBlock, &c4);
-  k_twin_fill<<<g, kBlock, 0, s>>>(tri, m, n, start, cnt, adj);
+  k_twin_fill<<<g, kBlock, 0, s>>>(tri, m, n, start, cnt, adj_dst, adj_he);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   g = resident_grid(reinterpret_cast<const void*>(k_twin_match), kBlock, 0,
                     (H + kBlock - 1) / kBlock, &c5);
   (void)sms;
-  k_twin_match<<<g, kBlock, 0, s>>>(tri, m, n, start, adj, twin, C);
+  k_twin_match<<<g, kBlock, 0, s>>>(tri, m, n, start, adj_dst, adj_he, twin, C);
   return cudaGetLastError();
 }
 

@@ -364,3 +364,11 @@ def test_twin_built_on_device_rejects_non_manifold():
     with pytest.raises(pg.PolyllaError) as e:
         pg.mesh_create(xy, t, None, 0)
     assert e.value.code == 3  # POLYLLA_ERR_TOPOLOGY
+    # an edge of three triangles (0->1 twice, with a 1->0), and a directed edge twice
+    # with no reverse (0->1 in two triangles on the same side)
+    pts = torch.tensor([[0, 0], [10, 0], [5, 5], [5, -5], [4, 8]], dtype=torch.int64).cuda()
+    for tris in ([[0, 1, 2], [1, 0, 3], [0, 1, 4]], [[0, 1, 2], [0, 1, 4]]):
+        t = torch.tensor(tris, dtype=torch.int32).cuda().contiguous()
+        with pytest.raises(pg.PolyllaError) as e:
+            pg.mesh_create(pts, t, None, 0)
+        assert e.value.code == 3, tris
