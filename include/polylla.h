@@ -74,7 +74,8 @@ typedef enum {
   POLYLLA_ERR_OOM = 4,         /* device allocation failed */
   POLYLLA_ERR_CUDA = 5,        /* a CUDA runtime call failed */
   POLYLLA_ERR_LIMIT = 6,       /* a walk or a reparation exceeded its bound */
-  POLYLLA_ERR_STATE = 7        /* phase called out of order */
+  POLYLLA_ERR_STATE = 7,       /* phase called out of order */
+  POLYLLA_ERR_CANCELLED = 8    /* served request cancelled before it was admitted */
 } polylla_status;
 
 #define POLYLLA_VALIDATE 1u /* mesh_create checks the mesh on the device (synchronises) */
@@ -383,8 +384,25 @@ polylla_status polylla_server_submit(polylla_server_t server, const int64_t* h_x
                                      int32_t* h_vtx_out, int64_t* id);
 int64_t polylla_server_poll(polylla_server_t server, polylla_result* out, int64_t cap,
                             int64_t wait_us);
+/*
+ * polylla_server_cancel: a request still queued (not yet admitted) is removed and
+ * completes at once with POLYLLA_ERR_CANCELLED (it is returned by the next poll);
+ * its host buffers are no longer used when the call returns.  A request already
+ * admitted, completed or unknown gives POLYLLA_ERR_STATE and runs to its end.
+ */
+polylla_status polylla_server_cancel(polylla_server_t server, int64_t id);
 polylla_status polylla_server_info(polylla_server_t server, polylla_server_stats* out);
 polylla_status polylla_server_destroy(polylla_server_t server);
+
+/*
+ * Failure injection for tests: the k-th device allocation the library makes from
+ * now on (counting every buffer of a handle, a batch or a server slot) fails as if
+ * the device were out of memory; k <= 0 turns it off.  Host-side only: the
+ * failing call returns before reaching the device.  Each entry point must then
+ * return POLYLLA_ERR_OOM (a served request: complete with it) and free what it
+ * had allocated.
+ */
+void polylla_debug_fail_alloc(int64_t k);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ LAB_TERMINAL = 0x40
 
 STATUS = {0: "POLYLLA_OK", 1: "POLYLLA_ERR_INVALID_ARG", 2: "POLYLLA_ERR_RANGE",
           3: "POLYLLA_ERR_TOPOLOGY", 4: "POLYLLA_ERR_OOM", 5: "POLYLLA_ERR_CUDA",
-          6: "POLYLLA_ERR_LIMIT", 7: "POLYLLA_ERR_STATE"}
+          6: "POLYLLA_ERR_LIMIT", 7: "POLYLLA_ERR_STATE", 8: "POLYLLA_ERR_CANCELLED"}
 
 
 class PolyllaError(RuntimeError):
@@ -129,6 +129,8 @@ def load_library(path: str | None = None):
             "polylla_server_submit": ([vp, vp, i64, vp, vp, i64, vp, vp, ctypes.POINTER(i64)], st),
             "polylla_server_poll": ([vp, ctypes.POINTER(Result), i64, i64], i64),
             "polylla_server_info": ([vp, ctypes.POINTER(ServerStats)], st),
+            "polylla_server_cancel": ([vp, i64], st),
+            "polylla_debug_fail_alloc": ([i64], None),
             "polylla_server_destroy": ([vp], st),
             "polylla_lepp": ([vp, vp], st),
             "polylla_mesh_build_twin": ([vp, vp], st),
@@ -481,6 +483,21 @@ def server_info(server: int) -> dict:
     return s.as_dict()
 
 
+def server_cancel(server: int, rid: int) -> bool:
+    """Cancel a queued request; False when it was already admitted (it runs on)."""
+    code = load_library().polylla_server_cancel(server, rid)
+    if code == 7:  # POLYLLA_ERR_STATE
+        return False
+    _check(code, "polylla_server_cancel")
+    return True
+
+
+def debug_fail_alloc(k: int):
+    """Failure injection for tests: the k-th device allocation from now on fails
+    (k <= 0: off)."""
+    load_library().polylla_debug_fail_alloc(k)
+
+
 def server_destroy(server: int):
     _check(load_library().polylla_server_destroy(server), "polylla_server_destroy")
 
@@ -613,6 +630,9 @@ class Server:
                 r["off"] = off[:r["n_poly"] + 1]
                 r["vtx"] = vtx[:r["n_vtx"]]
         return out
+
+    def cancel(self, rid: int) -> bool:
+        return server_cancel(self.handle, rid)
 
     def info(self) -> dict:
         return server_info(self.handle)

@@ -6,6 +6,7 @@
 // most m reparation pieces), so no phase allocates, synchronises or copies to the
 // host; phases only enqueue kernels on the caller's stream.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdio>
@@ -136,11 +137,27 @@ int grid_for(const polylla_mesh* h, long long units, int per_block) {
   return (int)blocks;
 }
 
+// failure injection (polylla_debug_fail_alloc): allocations left before the one
+// that fails; 0 when off
+std::atomic<long long> g_fail_alloc{0};
+
 template <class T>
 cudaError_t dalloc(T** p, long long count) {
+  if (g_fail_alloc.load(std::memory_order_relaxed) > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   if (count < 1) count = 1;
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)count);
 }
+
+// NVTX range over one phase (seen by profilers; a no-op without one)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 void free_all(polylla_mesh* h) {
   void* ptrs[] = {h->lab,      h->seeds,     h->succ,      h->tf,
@@ -304,6 +321,7 @@ polylla_status check_handle(polylla_mesh* h) {
 
 // ---------------------------------------------------------------- phases
 polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
+  const Range range("polylla label");
   const DevMesh& M = h->M;
   if (h->epoch >= 0x3ffffff0) {  // stamps: wrap around once in 2^30 runs
     POLY_TRY(cuda_status(cudaMemsetAsync(h->vstamp, 0, sizeof(int) * (size_t)M.n, s)));
@@ -327,6 +345,7 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
 }
 
 polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
+  const Range range("polylla seeds");
   const DevMesh& M = h->M;
   POLY_TRY(launch(h, "scan_seeds", s, [&] {
     return launch_scan_tiles(h->tile_sum, h->tile_off, M.m, nullptr, M.m, kTriTile,
@@ -343,6 +362,7 @@ polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
 // Walk every polygon (one thread, or one block for a long one) into the pool,
 // splitting those with tips when `repair`; then the CSR.
 polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long long* off, int* vtx) {
+  const Range range(repair ? "polylla repair" : "polylla traverse");
   const DevMesh& M = h->M;
   // counters of this pass start at zero (the traversal pass may have run before)
   const size_t first = offsetof(Counters, n_vtx_trav);
@@ -579,6 +599,8 @@ polylla_status batch_table(polylla_batch* b) {
 
 extern "C" {
 
+void polylla_debug_fail_alloc(int64_t k) { g_fail_alloc.store(k > 0 ? k : 0); }
+
 const char* polylla_status_str(polylla_status st) {
   switch (st) {
     case POLYLLA_OK: return "POLYLLA_OK";
@@ -589,6 +611,7 @@ const char* polylla_status_str(polylla_status st) {
     case POLYLLA_ERR_CUDA: return "POLYLLA_ERR_CUDA";
     case POLYLLA_ERR_LIMIT: return "POLYLLA_ERR_LIMIT";
     case POLYLLA_ERR_STATE: return "POLYLLA_ERR_STATE";
+    case POLYLLA_ERR_CANCELLED: return "POLYLLA_ERR_CANCELLED";
   }
   return "POLYLLA_ERR_UNKNOWN";
 }

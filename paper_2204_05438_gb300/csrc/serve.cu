@@ -362,6 +362,20 @@ int64_t polylla_server_poll(polylla_server_t S, polylla_result* out, int64_t cap
   return k;
 }
 
+polylla_status polylla_server_cancel(polylla_server_t S, int64_t id) {
+  if (!S) return POLYLLA_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->pending.begin();
+    while (it != S->pending.end() && it->id != id) ++it;
+    if (it == S->pending.end()) return POLYLLA_ERR_STATE;  // admitted, done or unknown
+    fail_pending(S, *it, POLYLLA_ERR_CANCELLED);
+    S->pending.erase(it);
+  }
+  S->cv_done.notify_all();
+  return POLYLLA_OK;
+}
+
 polylla_status polylla_server_info(polylla_server_t S, polylla_server_stats* out) {
   if (!S || !out) return POLYLLA_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(S->mu);

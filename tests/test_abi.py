@@ -109,6 +109,9 @@ def test_batch_argument_errors_need_no_device():
 
 def test_server_argument_errors_need_no_device():
     lib = pg.load_library()
+    assert lib.polylla_server_cancel(None, 1) == 1
+    assert pg.status_str(8) == "POLYLLA_ERR_CANCELLED"
+    pg.debug_fail_alloc(0)  # off: no effect
     s = ctypes.c_void_p(123)
     assert lib.polylla_server_create(1 << 30, 4, None) == 1
     assert lib.polylla_server_create(10, 4, ctypes.byref(s)) == 1
