@@ -142,6 +142,20 @@ __device__ __forceinline__ long long warp_alloc(long long* counter, int need) {
 }
 
 
+// Triangle of a seed's entry word (3t + k, or -1 - t)
+__device__ __forceinline__ long long entry_tri(int e) { return e >= 0 ? e / 3 : -1 - (long long)e; }
+
+// L2 prefetch of the whole 128-byte lines inside [p, p + bytes) (the partial
+// lines at either end are left out, so no address outside the range is touched),
+// spread over the block
+__device__ __forceinline__ void prefetch_l2(const void* p, long long bytes) {
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127;
+  const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + (uintptr_t)bytes) & ~(uintptr_t)127;
+  for (uintptr_t c = lo + 128 * (uintptr_t)threadIdx.x; c < hi; c += 128 * (uintptr_t)blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c));
+}
+
+
 __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
                                                        const int* __restrict__ entry,
                                                        const int* __restrict__ succ, PolyArrays P,
@@ -156,9 +170,22 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
   unsigned st_len = 0, st_tips = 0, st_tippolys = 0;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
-       base += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
     const long long i = base + threadIdx.x;
+    // the next iteration's seeds lie in one run of triangles (seeds ascend): the
+    // successor words of that run go to L2 now, while this iteration walks (the
+    // same for tri, or with a margin around the run, was slower)
+    if (base + stride < n) {
+      const long long nb = base + stride;
+      const long long ne = (nb + blockDim.x < n ? nb + blockDim.x : n) - 1;
+      const long long t0 = entry_tri(__ldg(entry + nb));
+      long long t1 = entry_tri(__ldg(entry + ne));
+      t1 = t1 >= M.m ? M.m - 1 : t1;
+      if (t1 >= t0) {
+        prefetch_l2(succ + 3 * t0, 12 * (t1 - t0 + 1));
+      }
+    }
     int len = 0, ntips = 0, tip_h = -1, rank0 = 0, start = 0;
     bool closed = false, is_long = false;
     if (i < n) {
