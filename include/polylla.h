@@ -345,7 +345,8 @@ polylla_status polylla_get_polygons_async(polylla_mesh_t mesh, const int64_t** d
  * with a device-memory budget (bytes, >= 1 MiB) and at most max_slots resident
  * slots.  A slot is a capacity handle for a size class (the smallest power of two
  * c >= max(4096, m, 2n) triangles, up to c/2 + 2 vertices) whose device state
- * stays allocated and serves the next request of its class.
+ * stays allocated and serves the next request of its class, or of a smaller
+ * class (up to 8x smaller) when no slot of that class is free.
  *
  * polylla_server_submit queues one mesh (host arrays as for polylla_run_host;
  * pinned memory lets the copies overlap; h_twin NULL: built on the device) and

@@ -7,9 +7,9 @@
 // buffers, output CSR -- stays allocated and is reused by the next request of
 // that class.  One worker thread:
 //   * admits pending requests in arrival order while a free slot of the right
-//     class exists or a new one fits the budget (idle slots of other classes are
-//     released to make room); a request whose class alone exceeds the budget
-//     fails with POLYLLA_ERR_OOM;
+//     class (or of a class up to 8x larger) exists or a new one fits the budget
+//     (idle slots of other classes are released to make room); a request whose
+//     class alone exceeds the budget fails with POLYLLA_ERR_OOM;
 //   * runs each admitted request on its slot's stream -- host-to-device copy of
 //     the inputs, the whole path (polylla_run), a copy of the output counts --
 //     so the requests that are admitted together overlap on the device;
@@ -227,12 +227,13 @@ bool step(polylla_server* S) {
       moved = true;
       continue;
     }
+    // an idle slot of the class, else of the smallest larger class up to 8x (a
+    // capacity handle serves any smaller mesh): a burst of one class then waits
+    // for no slot creation, whose allocations stall the device
     Slot* pick = nullptr;
     for (Slot* s : S->slots)
-      if (s->stage == 0 && s->cls == cls) {
+      if (s->stage == 0 && s->cls >= cls && s->cls <= 8 * cls && (!pick || s->cls < pick->cls))
         pick = s;
-        break;
-      }
     if (!pick) {
       // make room: release idle slots of other classes, oldest first
       while ((S->used + need > S->budget || (int)S->slots.size() >= S->max_slots)) {
