@@ -47,15 +47,14 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_TRAFFIC = {
     "sources": "9e4a4994ffaecadc",
     # one ncu --set full capture on gmm16-5m (9,999,947 triangles), scaled x2.0000 by
-    # triangle count to a gmm16-10m launch; taken at sources af5798c37c7df839 (then
-    # hashed over every CUDA file).  Since then the launchers' occupancy caches became
-    # atomic, k_seed_write, k_final_write and k_walk changed (their entries are
-    # dropped) and so did the twin construction, which the step does not run; the
-    # kernels listed here are unchanged
-    "bytes": {"succ": int((232.254720 + 105.280512) * 1e6 * 19999948 / 9999947),
-              "label_class": int((130.237952 + 80.135680) * 1e6 * 19999948 / 9999947),
-              "label_max": int((200.068352 + 8.713472) * 1e6 * 19999948 / 9999947),
-              "repair_one": int((134.258944 + 10.654464) * 1e6 * 19999948 / 9999947)},
+    # triangle count to a gmm16-10m launch
+    "bytes": {"walk": int((311.309568 + 62.932736) * 1e6 * 19999948 / 9999947),
+              "succ": int((232.313600 + 105.273344) * 1e6 * 19999948 / 9999947),
+              "out_write": int((90.000128 + 26.540544) * 1e6 * 19999948 / 9999947),
+              "label_class": int((130.235136 + 80.164864) * 1e6 * 19999948 / 9999947),
+              "label_max": int((200.070144 + 8.590336) * 1e6 * 19999948 / 9999947),
+              "seed_write": int((10.166016 + 0.000000) * 1e6 * 19999948 / 9999947),
+              "repair_one": int((134.179328 + 10.500352) * 1e6 * 19999948 / 9999947)},
 }
 
 
