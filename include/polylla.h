@@ -107,7 +107,7 @@ typedef struct {
  * VALIDATE the mesh is checked on the device (ids and twins in range, twin an
  * involution between reversed edges, coordinates in range, every triangle ccw
  * with positive area) and the call synchronises with `stream`.  Allocates every
- * derived buffer (about 200 bytes per triangle) so that later phases allocate
+ * derived buffer (about 190 bytes per triangle) so that later phases allocate
  * nothing.  On success *out receives the handle; on failure *out is NULL.
  */
 polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, const int32_t* d_tri,
