@@ -96,15 +96,15 @@ def algorithmic_bytes(name: str, s: dict) -> float:
         "label_max": 12 * m + 16 * n + m,
         # twin in, own and neighbour label bytes in, label byte and tf words out
         "label_class": 12 * m + 2 * m + 12 * m,
-        # label byte in, seed list out
-        "seed_write": m + 4 * ns,
+        # label byte in, seed list and each seed's entry half-edge out
+        "seed_write": m + 8 * ns,
         # label bytes and every tf word once, the successor of every frontier
         # half-edge out
         "succ": m + 12 * m + 4 * nv0,
-        # seed and its triangle's tf words, per vertex succ + origin in and pool out,
-        # per polygon its output record (count, length, pos), and start, length,
+        # per polygon its entry half-edge in and its output record (count, length,
+        # pos) out, per vertex succ + origin in and pool out, and start, length,
         # tips and tip for each polygon with tips
-        "walk": 16 * ns + 12 * nv0 + 16 * ns + 16 * s.get("ntp", 0),
+        "walk": 4 * ns + 12 * nv0 + 16 * ns + 16 * s.get("ntp", 0),
         # per polygon its piece count and length
         "out_tiles": 8 * ns,
         # per polygon record in, pool in, offsets and vertices out
