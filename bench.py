@@ -209,6 +209,8 @@ def run_ours(args, dist: Dist) -> dict | None:
     torch.cuda.set_device(dist.local_rank)
     dev = torch.device("cuda", dist.local_rank)
     mesh = meshgen.load(args.workload)
+    if args.shuffle is not None:  # locality stress: the same mesh, triangles in random order
+        mesh = meshgen.shuffled(mesh, args.shuffle)
     n, m = mesh["xy"].shape[0], mesh["tri"].shape[0]
     M = pg.from_numpy(mesh, device=str(dev), validate=True)
     stream = torch.cuda.current_stream(dev)
@@ -386,7 +388,9 @@ def run_ours(args, dist: Dist) -> dict | None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "points": n, "triangles": m,
+        "config": {"workload": args.workload + ("" if args.shuffle is None else
+                                                 f", triangles shuffled (seed {args.shuffle})"),
+                   "points": n, "triangles": m,
                    "generator": "SplitMix64 16-component Gaussian mixture on a 2^26 lattice, "
                                 "exact Delaunay (seed 2)",
                    "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
@@ -645,6 +649,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="gmm16-10m")
+    ap.add_argument("--shuffle", type=int, default=None,
+                    help="put the workload's triangles in a seeded random order (locality stress)")
     ap.add_argument("--kernel-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
