@@ -63,7 +63,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_final_write(PolyArrays P, FinalPi
 #pragma unroll
     for (int j = 0; j < kSub; ++j) {
       const long long i = tile * kOutTile + (long long)j * kPolyTile + threadIdx.x;
-      s_src[j][threadIdx.x] = i < n ? (pcj[j] == 0 ? P.pos[i] : F.pos[P.pbase[i]]) : -1;
+      const long long src = i < n ? (pcj[j] == 0 ? P.pos[i] : F.pos[P.pbase[i]]) : -1;
+      s_src[j][threadIdx.x] = src;
+      // the polygon's first vertex (and its line) to L2 while the tile waits for
+      // its look-back
+      if (src >= 0 && src < pool.cap) asm volatile("prefetch.global.L2 [%0];" ::"l"(pool.v + src));
       s_len[j][threadIdx.x] = lj[j];
       s_pc[j][threadIdx.x] = pcj[j];
       long long xc = i < n ? (pcj[j] == 0 ? 1 : pcj[j]) : 0, xl = lj[j];
