@@ -95,6 +95,18 @@ typedef struct {
   int64_t n_splits;       /* splits made by reparation */
   int64_t n_poly;         /* polygons after reparation */
   int64_t n_vtx;          /* their total length */
+  /* Which device path handled the polygons of the last traversal / reparation
+   * pass (every path gives the same polygons; these show which ones ran): */
+  int64_t n_long;         /* polygons longer than the thread walk's cap, walked by
+                             one thread block each */
+  int64_t n_long_handoff; /* of those, regions a small block could not hold and
+                             handed to a large one (batch schedules with long_mode 1, 2) */
+  int64_t n_long_seq;     /* of those, regions too large for any block's shared
+                             memory, walked and split by one thread */
+  int64_t n_one_tip;      /* polygons with exactly one tip, split by the one-tip kernel */
+  int64_t n_multi_tip;    /* polygons with several tips, split in shared memory */
+  int64_t n_multi_seq;    /* of those, polygons with more tips than the shared node
+                             list holds, split by re-walking */
 } polylla_stats;
 
 /*
@@ -219,11 +231,16 @@ int64_t polylla_launch_count(polylla_mesh_t mesh);
  *   d_lab: device uint8[n_tri], 4-byte aligned, receives the label bytes;
  *   d_seeds: device int32[n_tri] (capacity), receives the ascending seed list;
  *   d_n_seeds: one device int64, 8-byte aligned, receives the seed count.
- * The first call on a device looks up the scratch array's address for that device
- * and should be made before any stream capture.  Every call shares the one array
- * and clears what must start at zero, so calls that overlap on the GPU race and
- * must be serialised by the caller.  Synchronises with `stream` before returning,
- * to report device-side errors.
+ * The array and the entry point's kernels are loaded onto a device by the first
+ * call on that device (the CUDA runtime loads device code lazily): that first call
+ * allocates their device memory and may synchronise the device.  A caller that
+ * reserves all device memory for its own arena therefore makes one call (on any
+ * small mesh) per device before reserving it, and before any stream capture;
+ * later calls allocate nothing.  The array's address is looked up on every call
+ * with the calling device current.  Every call shares the one array and clears
+ * what must start at zero, so calls that overlap on the GPU race and must be
+ * serialised by the caller.  Each call waits for `stream` to finish before
+ * returning, to report device-side errors.
  */
 polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64_t n_vertices,
                                            const int32_t* d_tri, const int32_t* d_twin,

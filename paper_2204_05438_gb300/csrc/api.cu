@@ -768,10 +768,18 @@ polylla_status polylla_get_stats(polylla_mesh_t h, polylla_stats* out) {
     out->n_tip_polygons = c.n_tip_polys;
     out->n_tips = c.n_tips;
   }
+  if (h->phase >= kTraversed || h->latest_csr == 1) {
+    out->n_long = c.n_long;
+    out->n_long_handoff = c.n_long2;
+    out->n_long_seq = c.n_long_seq;
+  }
   if (h->phase >= kRepaired) {
     out->n_splits = c.n_splits;
     out->n_poly = c.n_poly;
     out->n_vtx = c.n_vtx;
+    out->n_one_tip = c.n_defer;
+    out->n_multi_tip = c.n_multi;
+    out->n_multi_seq = c.n_multi_seq;
   }
   return POLYLLA_OK;
 }

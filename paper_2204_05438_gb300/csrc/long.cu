@@ -157,6 +157,7 @@ __device__ void long_fallback(const DevMesh& M, uint8_t* lab, int* tf, int t0, l
   const long long limit = 3 * M.m + 3;
   P.pcnt[i] = 0;
   P.flen[i] = 0;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_long_seq), 1ull);
   const int e = region_entry_tf(tf, t0, H, limit);
   if (e < 0) {
     set_error(C, POLYLLA_ERR_LIMIT, 100);

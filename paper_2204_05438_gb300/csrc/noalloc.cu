@@ -16,20 +16,26 @@
 // Limits and sharing:
 //   * at most kNoAllocMaxTri = 2^26 triangles; larger meshes are rejected with
 //     POLYLLA_ERR_INVALID_ARG before anything is launched;
-//   * the scratch array (about 2 MiB) is part of the library image: every GPU that
-//     loads the library holds it until the process exits;
+//   * the scratch array (about 2 MiB) belongs to this file's device module.  The
+//     CUDA runtime loads modules lazily by default, so the array and the kernels
+//     are placed on a device by the first call on that device (its
+//     cudaGetSymbolAddress, or its first launch): that first call allocates the
+//     module's device memory and may synchronise the device.  A caller that
+//     reserves all device memory for its own arena makes one call (any small mesh)
+//     on each device before reserving it, and before any stream capture; after
+//     that no call allocates.  The module then stays loaded on that device until
+//     the process exits (or the caller resets the device);
 //   * every call on a device uses the same array and leaves its contents behind;
 //     the parts that must start at zero (the error word, the counters and the
 //     per-tile seed counts) are cleared at the start of each call, so
 //     consecutive calls are independent, but calls that overlap on the GPU (two
 //     streams, or two host threads at once) race on it and must be serialised by
 //     the caller;
-//   * the first call on a device looks up the array's device address (once per
-//     device, with that device current) and should come before any stream capture;
-//   * the call synchronises with `stream` before returning, to report errors that
-//     the kernels found on the device.
-#include <mutex>
-
+//   * the array's device address is looked up on every call, with the calling
+//     device current (a lookup, once the module is loaded), so a caller's
+//     cudaDeviceReset leaves no stale address behind;
+//   * each call waits for `stream` to finish its work before returning, to report
+//     errors that the kernels found on the device.
 #include "polylla_internal.cuh"
 
 using namespace polylla;
@@ -41,32 +47,20 @@ constexpr long long kNoAllocTiles = (kNoAllocMaxTri + kTriTile - 1) / kTriTile;
 constexpr size_t kTileBytes = sizeof(long long) * 2 * (size_t)kNoAllocTiles;
 constexpr size_t kCountersOffset = 2 * kTileBytes;
 constexpr size_t kScratchBytes = kCountersOffset + ((sizeof(Counters) + 255) / 256) * 256;
-constexpr int kMaxDevices = 64;
 
 // The whole scratch of this entry point: tile sums, tile offsets, counters.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_mu;
-unsigned char* g_scratch_dev[kMaxDevices] = {};
-int g_sms[kMaxDevices] = {};
-
-// Device address of the scratch array on `dev` (looked up once per device; the
-// host-side symbol g_noalloc_scratch is not a device address and is never
-// passed to a kernel).
+// Device address of the scratch array on the current device.  The host-side
+// symbol g_noalloc_scratch is not a device address and is never passed to a
+// kernel; cudaGetSymbolAddress gives the address in the current device's context.
 cudaError_t scratch_for(int dev, unsigned char** out, int* sms) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_dev[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    int n = 0;
-    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    g_sms[dev] = n;
-    g_scratch_dev[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_dev[dev];
-  *sms = g_sms[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
@@ -91,7 +85,7 @@ extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64
   if (((uintptr_t)d_xy | (uintptr_t)d_tri | (uintptr_t)d_twin) & 15u) return POLYLLA_ERR_INVALID_ARG;
   if (((uintptr_t)d_lab & 3u) || ((uintptr_t)d_n_seeds & 7u)) return POLYLLA_ERR_INVALID_ARG;
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return POLYLLA_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return POLYLLA_ERR_CUDA;
   unsigned char* base = nullptr;
   int sms = 0;
   if (scratch_for(dev, &base, &sms) != cudaSuccess) return POLYLLA_ERR_CUDA;

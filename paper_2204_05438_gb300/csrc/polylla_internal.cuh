@@ -44,6 +44,8 @@ struct Counters {
   long long n_multi;      // polygons with several tips, left to k_repair_multi
   long long ticket;       // tile tickets of the single-pass (look-back) scans
   long long n_long2;      // long polygons handed from the small blocks to the large ones
+  long long n_long_seq;   // long regions too large for a block, walked by one thread
+  long long n_multi_seq;  // several-tip polygons with more tips than the node list holds
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
   int error;              // first device error (polylla_status), 0 if none

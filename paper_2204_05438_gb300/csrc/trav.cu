@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
   const long long nd = min(C->n_multi, Dm.cap);
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
-  unsigned st_splits = 0;
+  unsigned st_splits = 0, st_seq = 0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < nd;
        base += (long long)gridDim.x * blockDim.x) {
     const long long d = base + t;
@@ -488,6 +488,7 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
     }
     int cnt;
     if (nt > kRsMaxSplit || L > kWalkCap || L < 3) {
+      ++st_seq;
       const Cyc first{P.start[i], L, P.tip_h[i], nt, true};
       cnt = repair_seq(M.tri, tf, lab, first, nt + 1, H, limit, F.h + foff, F.pos + foff,
                        F.len + foff, pool.v + off, off);
@@ -626,8 +627,11 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
     st_splits += cnt - 1;
   }
   st_splits = __reduce_add_sync(0xffffffffu, st_splits);
+  st_seq = __reduce_add_sync(0xffffffffu, st_seq);
   if ((threadIdx.x & 31) == 0 && st_splits)
     atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)st_splits);
+  if ((threadIdx.x & 31) == 0 && st_seq)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_multi_seq), (unsigned long long)st_seq);
 }
 
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,

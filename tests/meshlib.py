@@ -335,3 +335,92 @@ def tip_order_meshes():
     return [meshgen.generate("gmm", 16, 1 << 10, 18 * 7919 + 16),
             meshgen.generate("gmm", 60, 1 << 10, 32 * 7919 + 60),
             meshgen.generate("uniform", 60, 1 << 10, 52 * 7919 + 60)]
+
+
+# ------------------------------------------------------------------ hand-built regions
+def _mesh_from(xy, tri):
+    xy = np.asarray(xy, np.int64)
+    tri = np.asarray(tri, np.int32)
+    return {"xy": xy, "tri": tri, "twin": meshgen.twin_from_tri(tri)}
+
+
+def spiral_wheel(k: int, radius: int = 1 << 22, step: int = 64, center=(1 << 24, 1 << 24)):
+    """A fan of k triangles around one centre vertex (id 0) whose spokes grow
+    strictly with the angle (a spiral, rim vertex i at radius radius + i * step).
+    The rim is short next to the spokes, so each triangle's longest edge is its
+    later spoke: the longest-edge links run around the fan to the last spoke, which
+    is the longest of both its triangles (terminal), and the whole fan is one
+    terminal-edge region.  The first spoke is the longest of neither of its
+    triangles (frontier) with the region on both sides: a barrier edge whose tip is
+    the centre (Section 3.2.3).  Traversal gives one polygon of k + 2 vertices with
+    one tip; reparation splits it once."""
+    ang = 2 * np.pi * np.arange(k) / k
+    r = radius + step * np.arange(k)
+    rim = np.stack([np.rint(center[0] + r * np.cos(ang)), np.rint(center[1] + r * np.sin(ang))], 1)
+    xy = np.concatenate([np.array([center], np.float64), rim]).astype(np.int64)
+    i = np.arange(k)
+    tri = np.stack([np.zeros(k, np.int64), 1 + i, 1 + (i + 1) % k], 1)
+    return _mesh_from(xy, tri)
+
+
+def tip_hub(n_wheels: int = 9, hub_radius: int = 1 << 22, center=(1 << 24, 1 << 24)):
+    """One terminal-edge region with n_wheels + 1 barrier-edge tips and a short
+    boundary (6 n_wheels + 2 vertices): a spiral hub of n_wheels triangles around
+    vertex 0 (spokes growing by 2 % per step, so the hub's first spoke is a barrier
+    edge at the hub centre, as in spiral_wheel) and, glued outside each hub rim
+    edge, a small wheel of 5 triangles around its own centre.  A small wheel's
+    spokes grow ccw from one end of the hub edge to the other over four 50-degree
+    triangles; its fifth triangle is the flat one (about 160 degrees at the centre)
+    on the hub edge, whose longest edge is that hub edge.  The hub edge is not the
+    longest edge of the hub triangle, so it is internal, the small wheel's links
+    run into the hub, and its first spoke is a barrier edge whose tip is the wheel
+    centre."""
+    c = np.array(center, np.float64)
+    ang = 2 * np.pi * np.arange(n_wheels) / n_wheels
+    S = hub_radius * (1.0 + 0.02 * np.arange(n_wheels))
+    q = c + np.stack([S * np.cos(ang), S * np.sin(ang)], 1)
+    q = np.rint(q)
+    pts = [c] + list(q)  # 0: hub centre, 1..n: hub rim q_j
+    tri = [[0, 1 + j, 1 + (j + 1) % n_wheels] for j in range(n_wheels)]
+    for j in range(n_wheels):
+        a, b = q[j], q[(j + 1) % n_wheels]  # hub half-edge a -> b, hub on its left
+        d = b - a
+        e = np.hypot(*d)
+        u = d / e
+        out = np.array([u[1], -u[0]])  # right of a -> b: outside the hub
+        # the centre sees the hub edge under about 160 degrees, a little nearer a
+        cw = a + d * 0.47 + out * (0.5 * e / np.tan(np.radians(80.0)))
+        r0, r4 = np.hypot(*(a - cw)), np.hypot(*(b - cw))
+        a0 = np.arctan2(*(a - cw)[::-1])
+        a4 = np.arctan2(*(b - cw)[::-1])
+        span = (a4 - a0) % (2 * np.pi)  # ccw from a around the outside to b
+        ci = len(pts)
+        pts.append(np.rint(cw))
+        ids = [1 + j]
+        for i in (1, 2, 3):
+            th = a0 + span * i / 4
+            ri = r0 + (r4 - r0) * i / 4
+            ids.append(len(pts))
+            pts.append(np.rint(cw + ri * np.array([np.cos(th), np.sin(th)])))
+        ids.append(1 + (j + 1) % n_wheels)
+        for i in range(4):
+            tri.append([ci, ids[i], ids[i + 1]])
+        tri.append([ci, ids[4], ids[0]])
+    return _mesh_from(np.array(pts), tri)
+
+
+def disjoint_union(meshes, shift=(1 << 25, 0)):
+    """Several meshes side by side in one triangulation (vertex and half-edge ids
+    offset, coordinates shifted so the pieces do not overlap)."""
+    xy, tri, twin = [], [], []
+    nv = nh = 0
+    for j, mesh in enumerate(meshes):
+        xy.append(mesh["xy"] + np.array([shift[0] * j, shift[1] * j], np.int64))
+        tri.append(mesh["tri"] + nv)
+        tw = mesh["twin"].copy()
+        tw[tw >= 0] += nh
+        twin.append(tw)
+        nv += mesh["xy"].shape[0]
+        nh += 3 * mesh["tri"].shape[0]
+    return {"xy": np.concatenate(xy), "tri": np.concatenate(tri).astype(np.int32),
+            "twin": np.concatenate(twin).astype(np.int32)}

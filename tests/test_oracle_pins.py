@@ -13,7 +13,8 @@ import pytest
 import meshgen
 import oracle
 from meshlib import (brute_final_polygons, brute_labels, brute_regions, check_final_mesh,
-                     csr_to_lists, golden_cases, grid_mesh, lepp_end, tip_order_meshes, tips)
+                     csr_to_lists, golden_cases, grid_mesh, lepp_end, spiral_wheel, tip_hub,
+                     tip_order_meshes, tips)
 
 GOLDEN = golden_cases()
 
@@ -144,6 +145,44 @@ def test_bruteforce_small_with_tips():
         r = pin_bruteforce(mesh)
         seen += r["splits"]
     assert seen > 0
+
+
+@pytest.mark.parametrize("k", [7, 40, 5000])
+def test_spiral_wheel_is_one_region_with_one_tip(k):
+    """The hand-built fan of spiral_wheel (one region of k triangles, the centre a
+    barrier-edge tip): labels, regions and the final polygons from brute force,
+    and the traversal polygon of k + 2 vertices with its one tip, split once.  The
+    GPU tests rely on these properties to reach the one-thread walk of regions too
+    large for a thread block."""
+    mesh = spiral_wheel(k)
+    if k <= 40:
+        pin_bruteforce(mesh, convex=False)
+    r = oracle.full(mesh)
+    trav = csr_to_lists(r["trav_off"], r["trav_vtx"])
+    assert len(trav) == 1 and len(trav[0]) == k + 2
+    assert tips(trav[0]) == [0]
+    assert r["seeds"].tolist() == [k - 2]  # the lower triangle of the last spoke
+    polys, fr = brute_final_polygons(mesh)
+    assert csr_to_lists(r["off"], r["vtx"]) == polys
+    assert r["frontier_final"].tolist() == fr
+    assert r["splits"] == 1 and len(polys) == 2
+    check_final_mesh(mesh, polys, fr, convex=False)
+
+
+def test_tip_hub_has_ten_tips_on_a_short_boundary():
+    """tip_hub: one region whose boundary has 56 vertices and 10 tips (more than the
+    GPU's shared-memory node list holds, fewer vertices than its thread walk's
+    cap), pinned by brute force, with 10 splits."""
+    mesh = tip_hub()
+    pin_bruteforce(mesh, convex=False)
+    pin_repair_bruteforce(mesh)
+    r = oracle.full(mesh)
+    trav = csr_to_lists(r["trav_off"], r["trav_vtx"])
+    assert [len(p) for p in trav] == [56]
+    assert len(tips(trav[0])) == 10
+    assert r["splits"] == 10
+    polys, fr = brute_final_polygons(mesh)
+    check_final_mesh(mesh, polys, fr, convex=False)
 
 
 def test_invariants_uniform_1k():

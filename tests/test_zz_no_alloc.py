@@ -1,14 +1,21 @@
-"""The allocation-free entry point (polylla_label_seeds_noalloc), for callers that
-cannot allocate device memory: called through the C ABI twice in a row, its label
-bytes, seed list and seed count must equal those of the handle-based entry points
-(polylla_label + polylla_seeds) exactly -- the work is integer, so the tolerance
-is zero.  This file is collected last on purpose."""
+"""The allocation-free entry point (polylla_label_seeds_noalloc).
+
+It serves callers that cannot call cudaMalloc: an application that carves all
+device memory into its own arena at start-up, or code where an allocation's
+implicit device synchronisation would stall other work.  Its scratch lives in a
+fixed device array inside the library.  Called through the C ABI twice in a row,
+its label bytes, seed list and seed count must equal those of the handle-based
+entry points (polylla_label + polylla_seeds) and the CPU oracle's exactly -- the
+work is integer, so the tolerance is zero -- also when the caller's label array
+starts only 4 bytes into a larger buffer.  This file is collected last on purpose.
+"""
 from __future__ import annotations
 
 import numpy as np
 import pytest
 
 import meshgen
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -19,7 +26,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 import paper_2204_05438_gb300 as pg  # noqa: E402
 
 
-def _reference(mesh):
+def _handle_path(mesh):
     M = pg.from_numpy(mesh)
     M.label()
     M.seeds()
@@ -29,26 +36,48 @@ def _reference(mesh):
     return lab, seeds
 
 
+def _oracle_label_bytes(mesh):
+    """The label bytes as the library packs them, from the oracle's arrays."""
+    r = oracle.full(mesh)
+    lab = r["label"]
+    m = mesh["tri"].shape[0]
+    k = lab["max_edge"].astype(np.int64)
+    fr = lab["frontier"].reshape(m, 3).astype(np.int64)
+    term = lab["terminal"].reshape(m, 3)[np.arange(m), k].astype(np.int64)
+    packed = k | (fr[:, 0] << 2) | (fr[:, 1] << 3) | (fr[:, 2] << 4) | \
+        (lab["seed"].astype(np.int64) << 5) | (term << 6)
+    return packed.astype(np.uint8), r["seeds"]
+
+
 @pytest.mark.parametrize("mesh_fn", [
     lambda: meshgen.load("uniform-1k"),
     lambda: meshgen.generate("gmm", 200_003, 1 << 24, 21),
 ], ids=["uniform-1k", "gmm-200k"])
-def test_noalloc_matches_handle_path(mesh_fn):
+@pytest.mark.parametrize("lab_offset", [0, 4], ids=["aligned", "label-array-4-bytes-in"])
+def test_noalloc_matches_handle_path_and_oracle(mesh_fn, lab_offset):
     mesh = mesh_fn()
-    ref_lab, ref_seeds = _reference(mesh)
+    ref_lab, ref_seeds = _handle_path(mesh)
+    ora_lab, ora_seeds = _oracle_label_bytes(mesh)
+    assert np.array_equal(ref_lab, ora_lab) and np.array_equal(ref_seeds, ora_seeds)
     m = mesh["tri"].shape[0]
     xy = torch.as_tensor(mesh["xy"]).cuda().contiguous()
     tri = torch.as_tensor(mesh["tri"]).cuda().contiguous()
     twin = torch.as_tensor(mesh["twin"]).cuda().contiguous()
     for call in range(2):  # two calls in a row share the one scratch array
-        lab = torch.full((m,), 0xFF, dtype=torch.uint8, device="cuda")
+        big = torch.full((m + 16,), 0xFF, dtype=torch.uint8, device="cuda")
+        lab = big[lab_offset:lab_offset + m]
         seeds = torch.full((m,), -1, dtype=torch.int32, device="cuda")
         ns = torch.full((1,), -1, dtype=torch.int64, device="cuda")
         pg.label_seeds_noalloc(xy, tri, twin, lab, seeds, ns)
         k = int(ns.item())
+        got = lab.cpu().numpy()
         assert k == len(ref_seeds), f"call {call}: seed count"
-        assert np.array_equal(lab.cpu().numpy(), ref_lab), f"call {call}: label bytes"
-        assert np.array_equal(seeds[:k].cpu().numpy(), ref_seeds), f"call {call}: seed list"
+        assert np.array_equal(got, ref_lab), f"call {call}: label bytes"
+        assert np.array_equal(got, ora_lab), f"call {call}: label bytes against the oracle"
+        assert np.array_equal(seeds[:k].cpu().numpy(), ora_seeds), f"call {call}: seed list"
+        rest = big.cpu().numpy()
+        assert (rest[:lab_offset] == 0xFF).all() and (rest[lab_offset + m:] == 0xFF).all(), \
+            "bytes outside the label array were written"
 
 
 def test_noalloc_rejects_oversize():
