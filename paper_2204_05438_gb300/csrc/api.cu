@@ -281,6 +281,9 @@ long long derived_bytes(long long n, long long m) {
   COUNT(c.P.tip_h, m);
   c.Dm.cap = m;
   COUNT(c.Dm.poly, m);
+  COUNT(c.Lg2.poly, m);
+  COUNT(c.lepp_region, m);
+  COUNT(c.lepp_depth, m);
   COUNT(c.P.start, m);
   COUNT(c.P.len, m);
   COUNT(c.P.ntip, m);
