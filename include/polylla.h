@@ -127,6 +127,45 @@ polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, cons
                                    void* stream, polylla_mesh_t* out);
 
 /*
+ * Create a handle from the triangulator's Neighbor array instead of a twin array
+ * (Section 2: Triangle, QHull and Detri2 write it; the paper's inputs are
+ * Triangle's .node / .ele / .neigh files).  d_neighbor: device int32[3m],
+ * 4-byte aligned, borrowed for the call only; d_neighbor[3t + j] is the triangle
+ * across edge j of triangle t, or -1 on the border.  convention
+ * POLYLLA_NEIGHBOR_OPPOSITE: edge j is the edge opposite vertex tri[3t + j]
+ * (Triangle's .neigh layout); POLYLLA_NEIGHBOR_EDGE: edge j is the edge from
+ * tri[3t + j] to tri[3t + (j+1) % 3] (half-edge 3t + j).  The handle owns the
+ * twin array it builds on the device (the twin of u -> v is the neighbour's
+ * v -> u) and synchronises with `stream`; a neighbour id outside [-1, m) gives
+ * POLYLLA_ERR_RANGE, a neighbour without the reversed edge POLYLLA_ERR_TOPOLOGY.
+ * Otherwise as polylla_mesh_create (d_xy, d_tri 16-byte aligned; flags 0 or
+ * POLYLLA_VALIDATE).
+ *
+ * polylla_get_twin: the device twin array the handle uses (borrowed or built),
+ * valid until destroy.
+ */
+#define POLYLLA_NEIGHBOR_OPPOSITE 0
+#define POLYLLA_NEIGHBOR_EDGE 1
+polylla_status polylla_mesh_create_neighbors(const int64_t* d_xy, int64_t n_vertices,
+                                             const int32_t* d_tri, int64_t n_tri,
+                                             const int32_t* d_neighbor, int convention,
+                                             uint32_t flags, void* stream, polylla_mesh_t* out);
+polylla_status polylla_get_twin(polylla_mesh_t mesh, const int32_t** d_twin);
+
+/*
+ * The Trivertex array (Section 2: one element incident to each vertex; the
+ * paper's reparation finds a tip's fan through it, Section 3.2.3): for every
+ * vertex v, the smallest half-edge id leaving v (its triangle is id / 3), or -1
+ * for a vertex no triangle uses.  polylla_trivertex computes it on `stream`
+ * (asynchronous; any time after creation); polylla_get_trivertex (synchronises,
+ * reports a vertex id out of range) returns the handle-owned device int32[n],
+ * valid until the handle's triangles change or it is destroyed;
+ * POLYLLA_ERR_STATE before polylla_trivertex.
+ */
+polylla_status polylla_trivertex(polylla_mesh_t mesh, void* stream);
+polylla_status polylla_get_trivertex(polylla_mesh_t mesh, const int32_t** d_trivertex);
+
+/*
  * Label phase (Section 3.2.1, Algorithm 2): LabelMax, then LabelSeed and
  * LabelFrontier fused in one pass, writing lab[m] (layout above).  Restarts the
  * pipeline.  Asynchronous.
@@ -156,6 +195,21 @@ polylla_status polylla_traverse(polylla_mesh_t mesh, void* stream);
  * until no tips remain.  Writes the final CSR.  Asynchronous.
  */
 polylla_status polylla_repair(polylla_mesh_t mesh, void* stream);
+
+/*
+ * The reparation phase on the host: the paper's mixed variant (Section 3.2 and
+ * Section 4 compare GPU labelling and traversal followed by a sequential CPU
+ * reparation with the all-GPU path).  After polylla_traverse, copies the mesh, the
+ * label bytes and the traversal polygons to host memory, repairs them with one
+ * host thread (Section 3.2.3: each polygon's tips split in turn at the middle
+ * internal edge of the tip's fan, found through the Trivertex array; the same
+ * readings as polylla_repair), and copies the final polygons and label bytes
+ * back.  Afterwards the getters report exactly what they report after
+ * polylla_repair (the per-path counters of the device kernels stay 0).
+ * Synchronises; POLYLLA_ERR_STATE unless the last phase was polylla_traverse;
+ * POLYLLA_ERR_LIMIT if a polygon cannot be repaired (a corrupt mesh).
+ */
+polylla_status polylla_repair_host(polylla_mesh_t mesh, void* stream);
 
 /*
  * Algorithm 1 end to end: label, seeds, traversal and reparation.  The final

@@ -75,6 +75,8 @@ def _bind(path: str):
     lib.oracle_run.restype = i64
     lib.oracle_lepp.argtypes = [vp, i64, vp, vp, vp]
     lib.oracle_lepp.restype = i64
+    lib.oracle_trivertex.argtypes = [vp, i64, i64, vp]
+    lib.oracle_trivertex.restype = ctypes.c_int
     return lib
 
 
@@ -139,6 +141,17 @@ def lepp(mesh, max_edge: np.ndarray, lib=None):
     depth = np.zeros(m, np.int32)
     _check(lib.oracle_lepp(_p(twin), m, _p(max_edge), _p(region), _p(depth)))
     return region, depth
+
+
+def trivertex(mesh, lib=None) -> np.ndarray:
+    """The Trivertex array (Section 2): per vertex the smallest half-edge leaving
+    it, or -1 (int64[n])."""
+    lib = lib or _load()
+    xy, tri, _ = _mesh_arrays(mesh)
+    n, m = xy.shape[0], tri.shape[0]
+    tv = np.zeros(max(n, 1), np.int64)
+    _check(lib.oracle_trivertex(_p(tri), m, n, _p(tv)))
+    return tv[:n].copy()
 
 
 def traverse(mesh, frontier: np.ndarray, seed_list: np.ndarray, lib=None):

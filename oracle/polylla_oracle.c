@@ -310,6 +310,16 @@ static void build_trivertex(const int32_t* tri, int64_t m, int64_t n, int64_t* t
     if (tv[tri[h]] < 0) tv[tri[h]] = h;
 }
 
+/* The Trivertex array as a public routine (Section 2): tv[v] = the smallest
+ * half-edge leaving v, or -1 for a vertex no triangle uses.  Returns 0. */
+int oracle_trivertex(const int32_t* tri, int64_t m, int64_t n, int64_t* tv) {
+  if (!tri || !tv || m < 0 || n < 0) return ORACLE_ERR_ARG;
+  for (int64_t h = 0; h < 3 * m; ++h)
+    if (tri[h] < 0 || tri[h] >= n) return ORACLE_ERR_ARG;
+  build_trivertex(tri, m, n, tv);
+  return ORACLE_OK;
+}
+
 /* ccw successor of an out-half-edge o around its origin: twin(prev(o)) */
 static int64_t rot_ccw(const int32_t* twin, int64_t o) { return twin[he_prev(o)]; }
 

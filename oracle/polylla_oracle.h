@@ -26,6 +26,7 @@ int oracle_label_frontier(const int32_t* twin, int64_t m, const uint8_t* max_edg
 int64_t oracle_seed_list(const uint8_t* seed, int64_t m, int32_t* seeds);
 int64_t oracle_lepp(const int32_t* twin, int64_t m, const uint8_t* max_edge, int32_t* region,
                     int32_t* depth);
+int oracle_trivertex(const int32_t* tri, int64_t m, int64_t n, int64_t* tv);
 int64_t oracle_traverse(const int32_t* tri, const int32_t* twin, int64_t m, const uint8_t* frontier,
                         const int32_t* seeds, int64_t ns, int64_t* off, int32_t* vtx,
                         int64_t cap_vtx);

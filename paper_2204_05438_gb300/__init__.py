@@ -6,7 +6,8 @@ provides device memory and streams.  The functions mirror the C entry points:
 
     mesh_create, label, seeds, traverse, repair, run, get_labels, get_seeds,
     get_polygons, get_stats, mesh_destroy, status_str, mesh_create_host,
-    run_host, set_timing, kernel_times, launch_count, label_seeds_noalloc
+    run_host, set_timing, kernel_times, launch_count, label_seeds_noalloc,
+    mesh_create_neighbors, get_twin, trivertex, get_trivertex, repair_host
 
 There is no CPU fallback: if the library cannot be loaded every call raises.
 """
@@ -136,6 +137,12 @@ def load_library(path: str | None = None):
             "polylla_lepp": ([vp, vp], st),
             "polylla_mesh_build_twin": ([vp, vp], st),
             "polylla_get_lepp": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp)], st),
+            "polylla_mesh_create_neighbors": ([vp, i64, vp, i64, vp, i32, u32, vp,
+                                               ctypes.POINTER(vp)], st),
+            "polylla_get_twin": ([vp, ctypes.POINTER(vp)], st),
+            "polylla_trivertex": ([vp, vp], st),
+            "polylla_get_trivertex": ([vp, ctypes.POINTER(vp)], st),
+            "polylla_repair_host": ([vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -196,6 +203,43 @@ def mesh_create(xy: torch.Tensor, tri: torch.Tensor, twin: torch.Tensor | None,
     return h.value
 
 
+NEIGHBOR_OPPOSITE = 0
+NEIGHBOR_EDGE = 1
+
+
+def mesh_create_neighbors(xy: torch.Tensor, tri: torch.Tensor, neighbor: torch.Tensor,
+                          convention: int = NEIGHBOR_OPPOSITE, flags: int = VALIDATE,
+                          stream=None) -> int:
+    """polylla_mesh_create_neighbors: the twin array built on the device from the
+    triangulator's Neighbor array (int32 [m,3]; convention NEIGHBOR_OPPOSITE: entry
+    j across the edge opposite vertex j, as in Triangle's .neigh files)."""
+    lib = load_library()
+    n = xy.numel() // 2
+    m = tri.numel() // 3
+    h = ctypes.c_void_p()
+    _check(lib.polylla_mesh_create_neighbors(
+        _dptr(xy, torch.int64, "xy"), n, _dptr(tri, torch.int32, "tri"), m,
+        _dptr(neighbor, torch.int32, "neighbor"), convention, flags, _stream(stream),
+        ctypes.byref(h)), "polylla_mesh_create_neighbors")
+    return h.value
+
+
+def get_twin(mesh: int, m: int) -> torch.Tensor:
+    p = ctypes.c_void_p()
+    _check(load_library().polylla_get_twin(mesh, ctypes.byref(p)), "polylla_get_twin")
+    return _view(p.value, 3 * m, "<i4", torch.int32)
+
+
+def trivertex(mesh: int, stream=None):
+    _check(load_library().polylla_trivertex(mesh, _stream(stream)), "polylla_trivertex")
+
+
+def get_trivertex(mesh: int, n: int) -> torch.Tensor:
+    p = ctypes.c_void_p()
+    _check(load_library().polylla_get_trivertex(mesh, ctypes.byref(p)), "polylla_get_trivertex")
+    return _view(p.value, n, "<i4", torch.int32)
+
+
 def label(mesh: int, stream=None):
     _check(load_library().polylla_label(mesh, _stream(stream)), "polylla_label")
 
@@ -210,6 +254,12 @@ def traverse(mesh: int, stream=None):
 
 def repair(mesh: int, stream=None):
     _check(load_library().polylla_repair(mesh, _stream(stream)), "polylla_repair")
+
+
+def repair_host(mesh: int, stream=None):
+    """polylla_repair_host: the reparation phase on the host (the paper's mixed
+    variant), after traverse; synchronises."""
+    _check(load_library().polylla_repair_host(mesh, _stream(stream)), "polylla_repair_host")
 
 
 def run(mesh: int, stream=None):
@@ -524,6 +574,9 @@ class Mesh:
 
     def repair(self, stream=None):
         repair(self.handle, stream)
+
+    def repair_host(self, stream=None):
+        repair_host(self.handle, stream)
 
     def run(self, stream=None):
         run(self.handle, stream)

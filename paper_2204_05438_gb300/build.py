@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpolylla.so")
 BUILD_DIR = os.path.join(ROOT, "_build", "polylla")
 SOURCES = ["api.cu", "label.cu", "trav.cu", "long.cu", "final.cu", "noalloc.cu", "batch.cu",
-           "serve.cu", "lepp.cu", "twin.cu"]
+           "serve.cu", "lepp.cu", "twin.cu", "repair_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD_DIR, src.rsplit(".", 1)[0] + ".o")
         objs.append(obj)
         cmd = [cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:

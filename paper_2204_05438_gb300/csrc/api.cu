@@ -18,6 +18,12 @@
 
 using namespace polylla;
 
+namespace polylla {
+int64_t host_repair(int64_t n, int64_t m, const int32_t* tri, const int32_t* twin, uint8_t* lab,
+                    const int64_t* off, const int32_t* vtx, int64_t n_poly, int64_t* out_off,
+                    int32_t* out_vtx, int64_t* out_np, int64_t* out_nv);
+}
+
 namespace {
 
 enum Phase { kCreated = 0, kLabeled, kSeeded, kTraversed, kRepaired };
@@ -48,6 +54,8 @@ struct polylla_mesh {
   int* entry = nullptr;   // per seed: entry half-edge of its region (or -1 - t)
   int* lepp_region = nullptr;  // per triangle: seed of its longest-edge path's end
   int* lepp_depth = nullptr;   // per triangle: links of that path
+  int* trivertex = nullptr;    // per vertex: smallest half-edge leaving it, or -1
+  bool trivertex_valid = false;
   int* succ = nullptr;    // per frontier half-edge: boundary successor | tip flag
   int* tf = nullptr;      // twin | frontier bit, per half-edge (written by the label phase)
   int* loc = nullptr;     // per half-edge: member index inside a long-polygon block
@@ -79,6 +87,11 @@ struct polylla_mesh {
   int long_mode = 0;
   bool lepp_valid = false;
   long long* obase = nullptr;  // batches: output index of each traversal polygon
+
+  // host copies for polylla_repair_host (sized on first use)
+  std::vector<int32_t> h_tri, h_twin, h_vtx, h_out_vtx;
+  std::vector<uint8_t> h_lab;
+  std::vector<int64_t> h_off, h_out_off;
 
   bool timing = false;
   std::vector<TimingRec> recs;
@@ -167,7 +180,7 @@ void free_all(polylla_mesh* h) {
                   h->tile_sum, h->tile_off,  h->off_trav,  h->vtx_trav,   h->off_final,
                   h->vtx_final, h->C,         h->Dl.poly,   h->P.tip_h,
                   h->Dm.poly,   h->entry,     h->Lg2.poly,
-                  h->lepp_region, h->lepp_depth};
+                  h->lepp_region, h->lepp_depth, h->trivertex};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->owns_twin && !h->owns_inputs) cudaFree(const_cast<int*>(h->M.twin));
@@ -224,6 +237,7 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->entry, m);
   ALLOC(h->lepp_region, m);
   ALLOC(h->lepp_depth, m);
+  ALLOC(h->trivertex, n);
   ALLOC(h->tf, 3 * m);
   ALLOC(h->loc, 3 * m);
   ALLOC(h->vstamp, n);
@@ -284,6 +298,7 @@ long long derived_bytes(long long n, long long m) {
   COUNT(c.Lg2.poly, m);
   COUNT(c.lepp_region, m);
   COUNT(c.lepp_depth, m);
+  COUNT(c.trivertex, n);
   COUNT(c.P.start, m);
   COUNT(c.P.len, m);
   COUNT(c.P.ntip, m);
@@ -461,13 +476,24 @@ polylla_status do_build_twin(polylla_mesh* h, cudaStream_t s) {
   });
 }
 
-polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags) {
+// neigh (nullable): a Neighbor array (with its convention) the owned twin array is
+// built from, instead of from tri alone
+polylla_status create_common(polylla_mesh* h, cudaStream_t s, uint32_t flags,
+                             const int* neigh = nullptr, int convention = 0) {
   if (cudaGetDevice(&h->device) != cudaSuccess) return POLYLLA_ERR_CUDA;
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   POLY_TRY(alloc_derived(h));
   h->last_stream = s;
   if (h->owns_twin || h->owns_inputs) POLY_TRY(alloc_twin_scratch(h));
-  if (h->owns_twin) {  // built from tri now, and checked
+  if (h->owns_twin && neigh) {  // converted from the Neighbor array now, and checked
+    const int g = grid_for(h, h->M.m, kBlock);
+    POLY_TRY(launch(h, "twin_from_neighbor", s, [&] {
+      return launch_twin_from_neighbor(h->M.tri, neigh, h->M.m, convention,
+                                       const_cast<int*>(h->M.twin), h->C, g, s);
+    }));
+    Counters c;
+    POLY_TRY(read_counters(h, &c));
+  } else if (h->owns_twin) {  // built from tri now, and checked
     POLY_TRY(do_build_twin(h, s));
     Counters c;
     POLY_TRY(read_counters(h, &c));
@@ -653,6 +679,70 @@ polylla_status polylla_mesh_create(const int64_t* d_xy, int64_t n_vertices, cons
   return POLYLLA_OK;
 }
 
+polylla_status polylla_mesh_create_neighbors(const int64_t* d_xy, int64_t n_vertices,
+                                             const int32_t* d_tri, int64_t n_tri,
+                                             const int32_t* d_neighbor, int convention,
+                                             uint32_t flags, void* stream, polylla_mesh_t* out) {
+  if (!out) return POLYLLA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d_xy || !d_tri || !d_neighbor) return POLYLLA_ERR_INVALID_ARG;
+  if (convention != POLYLLA_NEIGHBOR_OPPOSITE && convention != POLYLLA_NEIGHBOR_EDGE)
+    return POLYLLA_ERR_INVALID_ARG;
+  if (n_vertices < 3 || n_vertices >= kMaxVertices || n_tri < 1 || n_tri >= kMaxTriangles)
+    return POLYLLA_ERR_INVALID_ARG;
+  if ((flags & ~POLYLLA_VALIDATE) != 0) return POLYLLA_ERR_INVALID_ARG;
+  if (((uintptr_t)d_xy | (uintptr_t)d_tri) & 15u) return POLYLLA_ERR_INVALID_ARG;
+  if ((uintptr_t)d_neighbor & 3u) return POLYLLA_ERR_INVALID_ARG;
+  polylla_mesh* h = new (std::nothrow) polylla_mesh();
+  if (!h) return POLYLLA_ERR_OOM;
+  h->M.xy = reinterpret_cast<const long long*>(d_xy);
+  h->M.tri = d_tri;
+  h->M.n = n_vertices;
+  h->M.m = n_tri;
+  int* tw = nullptr;
+  polylla_status st = cuda_status(dalloc(&tw, 3 * n_tri));
+  h->M.twin = tw;
+  h->owns_twin = true;
+  if (st == POLYLLA_OK)
+    st = create_common(h, (cudaStream_t)stream, flags, d_neighbor, convention);
+  if (st != POLYLLA_OK) {
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_get_twin(polylla_mesh_t h, const int32_t** d_twin) {
+  POLY_TRY(check_handle(h));
+  if (!d_twin) return POLYLLA_ERR_INVALID_ARG;
+  *d_twin = h->M.twin;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_trivertex(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  const int g = grid_for(h, 3 * h->M.m, kBlock);
+  POLY_TRY(launch(h, "trivertex", s, [&] {
+    return launch_trivertex(h->M.tri, h->M.m, h->M.n, h->trivertex, h->C, g, s);
+  }));
+  h->trivertex_valid = true;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_get_trivertex(polylla_mesh_t h, const int32_t** d_trivertex) {
+  POLY_TRY(check_handle(h));
+  if (!d_trivertex) return POLYLLA_ERR_INVALID_ARG;
+  if (!h->trivertex_valid) return POLYLLA_ERR_STATE;
+  Counters c;
+  POLY_TRY(read_counters(h, &c));  // syncs; reports an id out of range
+  *d_trivertex = h->trivertex;
+  return POLYLLA_OK;
+}
+
 polylla_status polylla_mesh_create_host(int64_t n_vertices, int64_t n_tri, polylla_mesh_t* out) {
   if (!out) return POLYLLA_ERR_INVALID_ARG;
   *out = nullptr;
@@ -707,6 +797,57 @@ polylla_status polylla_repair(polylla_mesh_t h, void* stream) {
   if (h->phase != kTraversed) return POLYLLA_ERR_STATE;
   h->last_stream = (cudaStream_t)stream;
   return do_repair(h, (cudaStream_t)stream);
+}
+
+polylla_status polylla_repair_host(polylla_mesh_t h, void* stream) {
+  POLY_TRY(check_handle(h));
+  if (h->phase != kTraversed) return POLYLLA_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  Counters c;
+  POLY_TRY(read_counters(h, &c));  // syncs; the traversal's errors first
+  const long long n = h->M.n, m = h->M.m, np = c.n_seeds, nv = c.n_vtx_trav;
+  try {
+    h->h_tri.resize((size_t)(3 * m));
+    h->h_twin.resize((size_t)(3 * m));
+    h->h_lab.resize((size_t)m);
+    h->h_off.resize((size_t)(np + 1));
+    h->h_vtx.resize((size_t)(nv > 0 ? nv : 1));
+    h->h_out_off.resize((size_t)(m + 1));
+    h->h_out_vtx.resize((size_t)(3 * m));
+  } catch (...) {
+    return POLYLLA_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpy(h->h_tri.data(), h->M.tri, sizeof(int) * 3 * m, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->h_twin.data(), h->M.twin, sizeof(int) * 3 * m, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(h->h_lab.data(), h->lab, (size_t)m, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->h_off.data(), h->off_trav, sizeof(long long) * (np + 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && nv > 0)
+    e = cudaMemcpy(h->h_vtx.data(), h->vtx_trav, sizeof(int) * nv, cudaMemcpyDeviceToHost);
+  POLY_TRY(cuda_status(e));
+  int64_t out_np = 0, out_nv = 0;
+  const int64_t splits =
+      host_repair(n, m, h->h_tri.data(), h->h_twin.data(), h->h_lab.data(), h->h_off.data(),
+                  h->h_vtx.data(), np, h->h_out_off.data(), h->h_out_vtx.data(), &out_np, &out_nv);
+  if (splits < 0) return POLYLLA_ERR_LIMIT;
+  e = cudaMemcpy(h->lab, h->h_lab.data(), (size_t)m, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->off_final, h->h_out_off.data(), sizeof(long long) * (out_np + 1),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && out_nv > 0)
+    e = cudaMemcpy(h->vtx_final, h->h_out_vtx.data(), sizeof(int) * out_nv, cudaMemcpyHostToDevice);
+  // the counters the getters report: splits, final polygons and their length
+  const long long cnt[3] = {splits, out_np, out_nv};
+  static_assert(offsetof(Counters, n_poly) == offsetof(Counters, n_splits) + sizeof(long long) &&
+                    offsetof(Counters, n_vtx) == offsetof(Counters, n_poly) + sizeof(long long),
+                "n_splits, n_poly and n_vtx are adjacent");
+  if (e == cudaSuccess) e = cudaMemcpy(&h->C->n_splits, cnt, sizeof(cnt), cudaMemcpyHostToDevice);
+  POLY_TRY(cuda_status(e));
+  h->phase = kRepaired;
+  h->latest_csr = 1;
+  return POLYLLA_OK;
 }
 
 polylla_status polylla_run(polylla_mesh_t h, void* stream) {
@@ -804,6 +945,7 @@ polylla_status polylla_run_host(polylla_mesh_t h, const int64_t* h_xy, const int
   if (!h_xy || !h_tri || !h_off || !h_vtx || !n_poly || !n_vtx) return POLYLLA_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const long long n = h->M.n, m = h->M.m;
+  h->trivertex_valid = false;
   cudaError_t e =
       cudaMemcpyAsync(const_cast<long long*>(h->M.xy), h_xy, sizeof(long long) * 2 * n,
                       cudaMemcpyHostToDevice, s);
@@ -910,6 +1052,7 @@ polylla_status polylla_mesh_set_size(polylla_mesh_t h, int64_t n_vertices, int64
   h->phase = kCreated;
   h->latest_csr = -1;
   h->lepp_valid = false;
+  h->trivertex_valid = false;
   return POLYLLA_OK;
 }
 

@@ -279,6 +279,13 @@ cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const 
 cudaError_t launch_build_twin(const int* tri, long long m, long long n, int* twin, int* cnt,
                               int* start, int2* adj, long long* tile_sum, long long* tile_off,
                               Counters* C, int sms, cudaStream_t s);
+// The twin array from a Neighbor array (convention 0: nb[3t+j] across the edge
+// opposite vertex j; 1: across the edge from vertex j to vertex j+1).
+cudaError_t launch_twin_from_neighbor(const int* tri, const int* nb, long long m, int convention,
+                                      int* twin, Counters* C, int grid, cudaStream_t s);
+// Trivertex: per vertex the smallest half-edge leaving it, or -1 (clears tv first).
+cudaError_t launch_trivertex(const int* tri, long long m, long long n, int* tv, Counters* C,
+                             int grid, cudaStream_t s);
 // Longest-edge propagation paths: per triangle its region's seed and the path length.
 cudaError_t launch_lepp(const DevMesh& M, const uint8_t* lab, int* region, int* depth, Counters* C,
                         int grid, cudaStream_t s);

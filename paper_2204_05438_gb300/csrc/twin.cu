@@ -190,3 +190,81 @@ cudaError_t launch_build_twin(const int* tri, long long m, long long n, int* twi
 }
 
 }  // namespace polylla
+
+namespace polylla {
+
+// ------------------------------------------------------------------ Neighbor array
+// The twin array from the triangulator's Neighbor array (Section 2): nb[3t + j] is
+// the triangle across edge j of t, or -1 on the border.  Edge j is the one
+// opposite vertex j (convention 0, the layout of Triangle's .neigh files) or the
+// one from vertex j to vertex j+1 (convention 1).  The twin of h = 3t + k (from
+// u = tri[h] to v = tri[3t + (k+1) % 3]) is the half-edge v -> u of that
+// neighbour; a neighbour id outside [-1, m) is POLYLLA_ERR_RANGE, a neighbour
+// without the reversed edge POLYLLA_ERR_TOPOLOGY (the twin is then -1).
+__global__ void __launch_bounds__(kBlock) k_twin_from_neighbor(const int* __restrict__ tri,
+                                                               const int* __restrict__ nb,
+                                                               long long m, int convention,
+                                                               int* __restrict__ twin,
+                                                               Counters* C) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a[3] = {__ldg(tri + 3 * t), __ldg(tri + 3 * t + 1), __ldg(tri + 3 * t + 2)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int j = convention ? k : (k + 2) % 3;  // the edge u -> v is opposite vertex k+2
+      const int u = __ldg(nb + 3 * t + j);
+      int g = -1;
+      if (u >= 0 && u < m) {
+        const int from = a[(k + 1) % 3], to = a[k];  // the twin runs v -> u
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (__ldg(tri + 3LL * u + q) == from && __ldg(tri + 3LL * u + (q + 1) % 3) == to)
+            g = 3 * u + q;
+        if (g < 0) set_error(C, POLYLLA_ERR_TOPOLOGY, 150);
+      } else if (u < -1 || u >= m) {
+        set_error(C, POLYLLA_ERR_RANGE, 151);
+      }
+      twin[3 * t + k] = g;
+    }
+  }
+}
+
+cudaError_t launch_twin_from_neighbor(const int* tri, const int* nb, long long m, int convention,
+                                      int* twin, Counters* C, int grid, cudaStream_t s) {
+  static std::atomic<int> cap{0};
+  grid = resident_grid(reinterpret_cast<const void*>(k_twin_from_neighbor), kBlock, 0, grid, &cap);
+  k_twin_from_neighbor<<<grid, kBlock, 0, s>>>(tri, nb, m, convention, twin, C);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Trivertex
+// The Trivertex array (Section 2: one element incident to each vertex; the
+// paper's reparation reaches a tip's fan through it): for every vertex, the
+// smallest half-edge leaving it, or -1 for a vertex no triangle uses.  tv starts
+// as all ones (0xffffffff = -1); each half-edge lowers its origin's word.
+__global__ void __launch_bounds__(kBlock) k_trivertex(const int* __restrict__ tri, long long m,
+                                                      long long n, unsigned* __restrict__ tv,
+                                                      Counters* C) {
+  const long long H = 3 * m;
+  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h < H;
+       h += (long long)gridDim.x * blockDim.x) {
+    const int v = __ldg(tri + h);
+    if (v < 0 || v >= n) {
+      set_error(C, POLYLLA_ERR_RANGE, 152);
+      continue;
+    }
+    atomicMin(tv + v, (unsigned)h);
+  }
+}
+
+cudaError_t launch_trivertex(const int* tri, long long m, long long n, int* tv, Counters* C,
+                             int grid, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(tv, 0xff, sizeof(int) * (size_t)n, s);
+  if (e != cudaSuccess) return e;
+  static std::atomic<int> cap{0};
+  grid = resident_grid(reinterpret_cast<const void*>(k_trivertex), kBlock, 0, grid, &cap);
+  k_trivertex<<<grid, kBlock, 0, s>>>(tri, m, n, reinterpret_cast<unsigned*>(tv), C);
+  return cudaGetLastError();
+}
+
+}  // namespace polylla

@@ -424,3 +424,15 @@ def disjoint_union(meshes, shift=(1 << 25, 0)):
         nh += 3 * mesh["tri"].shape[0]
     return {"xy": np.concatenate(xy), "tri": np.concatenate(tri).astype(np.int32),
             "twin": np.concatenate(twin).astype(np.int32)}
+
+
+def neighbors_from_twin(mesh, convention: int = 0) -> np.ndarray:
+    """The triangulator's Neighbor array (Section 2) of a mesh, from its twin
+    array: entry [t, j] is the triangle across edge j of t, or -1.  Convention 0:
+    edge j is opposite vertex j (Triangle's .neigh files), i.e. half-edge
+    3t + (j + 1) % 3; convention 1: edge j is half-edge 3t + j."""
+    twin = np.asarray(mesh["twin"], np.int64).reshape(-1, 3)
+    cross = np.where(twin >= 0, twin // 3, -1)
+    if convention == 0:
+        cross = cross[:, [1, 2, 0]]
+    return np.ascontiguousarray(cross.astype(np.int32))

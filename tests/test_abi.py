@@ -61,6 +61,16 @@ def test_argument_errors_need_no_device():
     assert lib.polylla_mesh_create(16, 10, 16, 10, 16, 8, None, ctypes.byref(h)) == 1
     assert lib.polylla_mesh_create(20, 10, 16, 10, 16, 0, None, ctypes.byref(h)) == 1  # misaligned
     assert lib.polylla_label(None, None) == 1
+    # the Neighbor-array entry point: null pointers, an unknown convention, misalignment
+    create_nb = lib.polylla_mesh_create_neighbors
+    create_nb.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                          ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
+                          ctypes.c_void_p]
+    assert create_nb(None, 10, None, 10, None, 0, 0, None, ctypes.byref(h)) == 1
+    assert create_nb(16, 10, 16, 10, 16, 2, 0, None, ctypes.byref(h)) == 1
+    assert create_nb(16, 10, 16, 10, 18, 0, 0, None, ctypes.byref(h)) == 1
+    assert lib.polylla_get_twin(None, None) == 1
+    assert lib.polylla_trivertex(None, None) == 1
     assert lib.polylla_mesh_destroy(None) == 1
     assert lib.polylla_launch_count(None) == -1
 

@@ -185,6 +185,22 @@ def test_tip_hub_has_ten_tips_on_a_short_boundary():
     check_final_mesh(mesh, polys, fr, convex=False)
 
 
+def test_trivertex_bruteforce():
+    """The oracle's Trivertex array (Section 2): for every vertex the smallest
+    half-edge leaving it, -1 for an unused vertex, against a direct search."""
+    meshes = list(TINY[:20]) + [c["mesh"] for c in GOLDEN]
+    base = TINY[3]
+    extra = np.array([[(1 << 20) + 5, 9], [(1 << 20) + 7, 3]], np.int64)
+    meshes.append({"xy": np.concatenate([base["xy"], extra]), "tri": base["tri"],
+                   "twin": base["twin"]})  # two vertices no triangle uses
+    for mesh in meshes:
+        tv = oracle.trivertex(mesh)
+        tri = np.asarray(mesh["tri"]).reshape(-1).tolist()
+        for v in range(mesh["xy"].shape[0]):
+            hs = [h for h, w in enumerate(tri) if w == v]
+            assert tv[v] == (min(hs) if hs else -1), v
+
+
 def test_invariants_uniform_1k():
     mesh = meshgen.load("uniform-1k")
     r = oracle.full(mesh)
