@@ -97,8 +97,9 @@ typedef struct {
   int64_t n_vtx;          /* their total length */
   /* Which device path handled the polygons of the last traversal / reparation
    * pass (every path gives the same polygons; these show which ones ran): */
-  int64_t n_long;         /* polygons longer than the thread walk's cap, walked by
-                             one thread block each */
+  int64_t n_long;         /* polygons longer than the thread walk's cap (and, on
+                             meshes of fewer than 2^16 triangles, polygons with three
+                             or more tips), walked and split by one thread block each */
   int64_t n_long_handoff; /* of those, regions a small block could not hold and
                              handed to a large one (batch schedules with long_mode 1, 2) */
   int64_t n_long_seq;     /* of those, regions too large for any block's shared
@@ -276,9 +277,9 @@ int64_t polylla_launch_count(polylla_mesh_t mesh);
  * that owns the whole device heap, or code that must not let cudaMalloc /
  * cudaFree synchronise the device).  It computes exactly what polylla_label
  * followed by polylla_seeds computes, without a handle, and allocates nothing:
- * its only scratch (per-tile seed counts and offsets, and an error word) lives in
- * a fixed file-scope device array of about 2 MiB, which every GPU that loads the
- * library holds until the process exits.
+ * its only scratch (the seed compaction's look-back words, counters and an error
+ * word) lives in a fixed file-scope device array of about 33 KiB, which every GPU
+ * that loads the library holds until the process exits.
  *   d_xy, n_vertices, d_tri, d_twin, n_tri: the mesh, as for polylla_mesh_create
  *     (16-byte aligned), with at most 2^26 triangles -- larger meshes are rejected
  *     with POLYLLA_ERR_INVALID_ARG;

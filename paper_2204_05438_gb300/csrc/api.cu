@@ -68,8 +68,10 @@ struct polylla_mesh {
   LongList Dm{};          // polygons with several tips
   LongList Lg2{};         // long polygons the small blocks hand to the large ones
   int epoch = 0;
-  long long* tile_sum = nullptr;
+  long long* tile_sum = nullptr;  // twin construction: per-tile counts and offsets
   long long* tile_off = nullptr;
+  unsigned long long* seed_status = nullptr;  // look-back words of the seed pass
+  unsigned long long* out_status = nullptr;   // look-back words of the output pass
   long long* off_trav = nullptr;
   int* vtx_trav = nullptr;
   long long* off_final = nullptr;
@@ -178,6 +180,7 @@ void free_all(polylla_mesh* h) {
                   h->P.ntip,   h->P.pcnt,    h->P.pbase,    h->P.flen,
                   h->P.pos,    h->F.pos,     h->F.len,     h->F.h,        h->pool.v,
                   h->tile_sum, h->tile_off,  h->off_trav,  h->vtx_trav,   h->off_final,
+                  h->seed_status, h->out_status,
                   h->vtx_final, h->C,         h->Dl.poly,   h->P.tip_h,
                   h->Dm.poly,   h->entry,     h->Lg2.poly,
                   h->lepp_region, h->lepp_depth, h->trivertex};
@@ -261,6 +264,8 @@ polylla_status alloc_derived(polylla_mesh* h) {
   ALLOC(h->pool.v, h->pool.cap);
   ALLOC(h->tile_sum, 2 * ntiles);
   ALLOC(h->tile_off, 2 * ntiles);
+  ALLOC(h->seed_status, seed_tiles(m) + 1);
+  ALLOC(h->out_status, ntiles + 1);
   ALLOC(h->off_trav, m + 1);
   ALLOC(h->vtx_trav, 3 * m);
   ALLOC(h->off_final, m + 1);
@@ -269,6 +274,11 @@ polylla_status alloc_derived(polylla_mesh* h) {
 #undef ALLOC
   // stamped arrays start empty (run stamps are never 0)
   if (e == cudaSuccess) e = cudaMemset(h->vstamp, 0, sizeof(int) * (size_t)n);
+  // look-back words start zero (each pass leaves them zero)
+  if (e == cudaSuccess)
+    e = cudaMemset(h->seed_status, 0, sizeof(unsigned long long) * (size_t)(seed_tiles(m) + 1));
+  if (e == cudaSuccess)
+    e = cudaMemset(h->out_status, 0, sizeof(unsigned long long) * (size_t)(ntiles + 1));
   if (e == cudaSuccess) e = cudaMemset(h->C, 0, sizeof(Counters));
   return cuda_status(e);
 }
@@ -312,6 +322,8 @@ long long derived_bytes(long long n, long long m) {
   COUNT(c.pool.v, c.pool.cap);
   COUNT(c.tile_sum, 2 * ntiles);
   COUNT(c.tile_off, 2 * ntiles);
+  COUNT(c.seed_status, seed_tiles(m) + 1);
+  COUNT(c.out_status, ntiles + 1);
   COUNT(c.off_trav, m + 1);
   COUNT(c.vtx_trav, 3 * m);
   COUNT(c.off_final, m + 1);
@@ -350,11 +362,8 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   const int g1 = grid_for(h, (M.m + 3) / 4, kBlock);
   POLY_TRY(launch(h, "label_max", s, [&] { return launch_label_max(M, h->lab, h->C, g1, s); }));
   const int g2 = grid_for(h, M.m, kTriTile);
-  // per-tile seed counts are accumulated by atomics
-  const long long ntiles = (M.m + kTriTile - 1) / kTriTile;
-  POLY_TRY(cuda_status(cudaMemsetAsync(h->tile_sum, 0, 2 * sizeof(long long) * (size_t)ntiles, s)));
   POLY_TRY(launch(h, "label_class", s, [&] {
-    return launch_label_class(M, h->lab, h->tile_sum, h->tf, h->C, g2, s);
+    return launch_label_class(M, h->lab, h->tf, h->C, g2, s);
   }));
   h->phase = kLabeled;
   h->lepp_valid = false;
@@ -365,13 +374,9 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
 polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
   const Range range("polylla seeds");
   const DevMesh& M = h->M;
-  POLY_TRY(launch(h, "scan_seeds", s, [&] {
-    return launch_scan_tiles(h->tile_sum, h->tile_off, M.m, nullptr, M.m, kTriTile,
-                             &h->C->n_seeds, &h->C->scratch0, nullptr, 0, 0, h->C, s);
-  }));
-  const int g = grid_for(h, M.m, kTriTile);
+  const int g = grid_for(h, M.m, 16 * kTriTile);
   POLY_TRY(launch(h, "seed_write", s, [&] {
-    return launch_seed_write(h->lab, M.m, h->tile_off, h->seeds, h->entry, g, s);
+    return launch_seed_write(h->lab, M.m, h->seed_status, h->seeds, h->entry, h->C, g, s);
   }));
   h->phase = kSeeded;
   return POLYLLA_OK;
@@ -382,10 +387,13 @@ polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
 polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long long* off, int* vtx) {
   const Range range(repair ? "polylla repair" : "polylla traverse");
   const DevMesh& M = h->M;
-  // counters of this pass start at zero (the traversal pass may have run before)
-  const size_t first = offsetof(Counters, n_vtx_trav);
-  const size_t last = offsetof(Counters, scratch0);
-  POLY_TRY(cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(h->C) + first, 0, last - first, s)));
+  // counters of this pass start at zero: right after the seeds they are (the label
+  // phase cleared them); after a traversal pass they are cleared here
+  if (h->phase != kSeeded) {
+    const size_t first = offsetof(Counters, n_vtx_trav);
+    const size_t last = offsetof(Counters, seed_ticket);
+    POLY_TRY(cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(h->C) + first, 0, last - first, s)));
+  }
   if (repair == 0 || h->phase < kTraversed) {
     const int gt = grid_for(h, M.m, kBlock);
     POLY_TRY(launch(h, "succ", s, [&] {
@@ -395,7 +403,7 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   const int gw = grid_for(h, M.m, 4 * 256);
   POLY_TRY(launch(h, "walk", s, [&] {
     return launch_walk(M, h->tf, h->entry, h->succ, h->P, h->pool, h->Lg, h->Dl, h->Dm,
-                       h->walk_cap, repair, h->C, gw, s);
+                       h->walk_cap, repair, M.m < kSmallMeshTri ? 3 : 0, h->C, gw, s);
   }));
   // repair_one (this stream), repair_multi and long (side streams) at once
   const bool fork = !h->timing && h->overlap;
@@ -428,15 +436,12 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
       POLY_TRY(cuda_status(cudaStreamWaitEvent(s, h->join[k], 0)));
     }
   }
-  // one pass: offsets by look-back (status words zeroed; the ticket counter was
-  // reset with the pass's counters)
+  // one pass: offsets by look-back (the status words are zero; the ticket counter
+  // starts at zero with the pass's counters)
   const int gt = grid_for(h, M.m, kPolyTile);
-  const long long ntiles = (M.m + kPolyTile - 1) / kPolyTile;
-  unsigned long long* status = reinterpret_cast<unsigned long long*>(h->tile_sum);
-  POLY_TRY(cuda_status(
-      cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)ntiles, s)));
   return launch(h, "out_write", s, [&] {
-    return launch_final_write(h->P, h->F, h->pool, status, off, vtx, h->obase, M.m, h->C, gt, s);
+    return launch_final_write(h->P, h->F, h->pool, h->out_status, off, vtx, h->obase, M.m, h->C,
+                              gt, s);
   });
 }
 

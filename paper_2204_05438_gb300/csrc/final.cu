@@ -28,7 +28,8 @@ __device__ __forceinline__ void out_counts(const PolyArrays& P, long long i, lon
 // offsets come from a look-back over `status` in the same pass (tiles in ticket
 // order; one word per tile packs the piece count << 33 | vertex count, exact
 // within the mesh size limits), and the last tile writes the totals and the CSR
-// end marker.
+// end marker.  The status words clean themselves: the block that completes the
+// last look-back (C->out_done counts them) clears them and the count.
 constexpr int kSub = 4;
 constexpr int kOutTile = kSub * kPolyTile;
 
@@ -43,6 +44,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_final_write(PolyArrays P, FinalPi
   __shared__ long long s_xc[kSub][kBlock], s_xl[kSub][kBlock];  // in-warp exclusive sums
   __shared__ long long s_wc[kBlock / 32][kSub], s_wl[kBlock / 32][kSub];  // warp sums
   __shared__ long long s_tile, s_p, s_v;
+  __shared__ int s_clear;
   const long long n = C->n_seeds;
   const long long ntiles = (n + kOutTile - 1) / kOutTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -100,6 +102,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_final_write(PolyArrays P, FinalPi
       if (threadIdx.x == 0) {
         s_p = ex >> 33;
         s_v = ex & ((1ll << 33) - 1);
+        // the last look-back to complete clears the status words for the next pass
+        const unsigned long long done =
+            atomicAdd(reinterpret_cast<unsigned long long*>(&C->out_done), 1ull);
+        s_clear = done == (unsigned long long)(ntiles - 1);
         if (tile == ntiles - 1) {
           const long long np = s_p + ac, nv = s_v + al;
           C->n_poly = np;
@@ -176,6 +182,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_final_write(PolyArrays P, FinalPi
             if (k + 32 * u < run) to[k + 32 * u] = v[u];
         }
       }
+    }
+    if (s_clear) {  // every tile has finished its look-back
+      for (long long q = threadIdx.x; q < ntiles; q += kBlock) status[q] = 0;
+      if (threadIdx.x == 0) C->out_done = 0;
     }
     __syncthreads();
   }

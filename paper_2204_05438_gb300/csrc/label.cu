@@ -3,9 +3,9 @@
 //   k_label_max    LabelMax: per triangle, the index of its longest edge.
 //   k_label_class  LabelSeed + LabelFrontier fused: per triangle, the frontier
 //                  flag of each edge, "longest edge is terminal" and the seed
-//                  flag, plus the seed count of every 1024-triangle tile.
-//   k_seed_write   the Seed array compacted in ascending order (tile offsets
-//                  come from the scan of the tile counts).
+//                  flag.
+//   k_seed_write   the Seed array compacted in ascending order, the tile
+//                  offsets by a decoupled look-back in the same pass.
 //
 // All three are HBM streams over the triangle arrays (tri / twin: 12 bytes per
 // triangle each, read as 3 x int4 per thread of 4 triangles) with gathers of
@@ -162,12 +162,9 @@ cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int gr
 // rewrite keeps those bits, so any version of a byte gives the same answer.
 // When tf is given, also writes tf[h] = twin(h) with bit 31 set iff h is frontier
 // (0x7fffffff as the twin of a border half-edge): one load then tells both
-// whether a walk stops at h and where it turns next.
-// The seed counts are summed per warp and added to the tile's count with one
-// atomic (tile_sum zeroed beforehand), so no barrier holds a block to its slowest
-// warp.
+// whether a walk stops at h and where it turns next.  No barrier: each thread's 4
+// triangles are independent.
 __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* lab,
-                                                           long long* __restrict__ tile_sum,
                                                            int* __restrict__ tf, Counters* C) {
   const long long m = M.m;
   const long long H = 3 * m;
@@ -175,7 +172,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* l
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long g = tile * kBlock + threadIdx.x;  // group of 4 triangles
     const long long t0 = 4 * g;
-    int nseed = 0;
     if (t0 < m) {
       int tw[12];
       load_tri_group(M.twin, g, m, tw);
@@ -216,7 +212,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* l
         const bool seed = terminal && (gs < 0 || t < gs / 3);
         byte |= (unsigned)terminal << 6;
         byte |= (unsigned)seed << 5;
-        nseed += seed;
         out |= byte << (8 * j);
       }
       if (full) {
@@ -235,101 +230,159 @@ __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* l
         }
       }
     }
-    const int tot = __reduce_add_sync(0xffffffffu, nseed);
-    if ((threadIdx.x & 31) == 0 && tot)
-      atomicAdd(reinterpret_cast<unsigned long long*>(tile_sum + 2 * tile), (unsigned long long)tot);
   }
 }
 
-cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, int* tf,
-                               Counters* C, int grid, cudaStream_t s) {
+cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, int* tf, Counters* C, int grid,
+                               cudaStream_t s) {
   static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_label_class), kBlock, 0, grid, &cap);
-  k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tile_sum, tf, C);
+  k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tf, C);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ seed compaction
+// The Seed array compacted in ascending order in one pass: a block takes, in
+// ticket order, tiles of kSeedSub sub-tiles of kSeedSpan triangles (16 per thread
+// and sub-tile, one 16-byte label load each), counts their seeds (label bit 5),
+// gets the tile's offset by a decoupled look-back over `status` (one word per
+// tile), and writes each sub-tile's seeds -- staged in shared memory -- coalesced.
+// The last tile writes the seed count to C->n_seeds.  The status words clean
+// themselves: the block that completes the last look-back (C->seed_done counts
+// them) clears them and the count, so nothing has to be zeroed before the next
+// run; the ticket counter C->seed_ticket starts at zero with the label phase's
+// counters.
 // With `entry` non-null, also the entry half-edge of each seed's region for the
 // walk: 3t + k for the first frontier edge k of t (label bits 2-4), or -1 - t when
 // t has no frontier edge (the walk then turns around t's first vertex).
+constexpr int kSeedPer = 16;
+constexpr int kSeedSpan = kBlock * kSeedPer;   // triangles per sub-tile
+constexpr int kSeedSub = 4;                    // sub-tiles per look-back tile
+constexpr int kSeedTile = kSeedSub * kSeedSpan;
+
 __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict__ lab, long long m,
-                                                       const long long* __restrict__ tile_off,
+                                                       unsigned long long* status,
                                                        int* __restrict__ seeds,
-                                                       int* __restrict__ entry) {
-  // 16 triangles per thread (one 16-byte label load): a block covers four
-  // consecutive 1024-triangle tiles, whose seeds are one contiguous run of the
-  // output; they are staged in shared memory and written out coalesced
-  constexpr int kPer = 16;
-  constexpr int kTilesPerBlock = kBlock * kPer / kTriTile;
-  constexpr int kSpan = kBlock * kPer;
-  __shared__ int sw[kBlock / 32];
-  __shared__ int s_seed[kSpan], s_entry[kSpan];
+                                                       int* __restrict__ entry, Counters* C) {
+  __shared__ int sw[kSeedSub][kBlock / 32];
+  __shared__ int s_seed[kSeedSpan], s_entry[kSeedSpan];
+  __shared__ long long s_tile, s_base;
+  __shared__ int s_clear;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long nbt = (m + kSpan - 1) / kSpan;
+  const long long nbt = (m + kSeedTile - 1) / kSeedTile;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(lab) & 15u) == 0;
-  for (long long bt = blockIdx.x; bt < nbt; bt += gridDim.x) {
-    const long long t0 = (bt * kBlock + threadIdx.x) * kPer;
-    const long long base = tile_off[2 * (bt * kTilesPerBlock)];
-    unsigned w[4] = {0, 0, 0, 0};
-    if (t0 + kPer <= m && aligned16) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(lab) + (t0 / kPer));
-      w[0] = v.x;
-      w[1] = v.y;
-      w[2] = v.z;
-      w[3] = v.w;
-    } else if (t0 + kPer <= m) {  // a caller's label array aligned to 4 bytes only
-      const unsigned* l4 = reinterpret_cast<const unsigned*>(lab + t0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) w[q] = __ldg(l4 + q);
-    } else {
-      for (int j = 0; j < kPer && t0 + j < m; ++j) w[j >> 2] |= (unsigned)__ldg(lab + t0 + j) << (8 * (j & 3));
-    }
-    unsigned smask = 0;  // bit i: triangle t0 + i is a seed
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) smask |= ((w[i >> 2] >> (8 * (i & 3) + 5)) & 1u) << i;
-    const int cnt = __popc(smask);
-    int incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += y;
-    }
-    if (lane == 31) sw[warp] = incl;
+  for (;;) {
+    if (threadIdx.x == 0)
+      s_tile = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->seed_ticket), 1ull);
     __syncthreads();
-    int before = 0, total = 0;
+    const long long bt = s_tile;
+    if (bt >= nbt) break;
+    // this thread's 16 label bytes of each sub-tile (every load issued first)
+    unsigned w[kSeedSub][4];
+    unsigned smask[kSeedSub];
+    int incl[kSeedSub], cnt[kSeedSub];
 #pragma unroll
-    for (int v = 0; v < kBlock / 32; ++v) {
-      before += (v < warp) ? sw[v] : 0;
-      total += sw[v];
+    for (int j = 0; j < kSeedSub; ++j) {
+      const long long t0 = ((bt * kSeedSub + j) * kBlock + threadIdx.x) * kSeedPer;
+      w[j][0] = w[j][1] = w[j][2] = w[j][3] = 0;
+      if (t0 + kSeedPer <= m && aligned16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(lab) + (t0 / kSeedPer));
+        w[j][0] = v.x;
+        w[j][1] = v.y;
+        w[j][2] = v.z;
+        w[j][3] = v.w;
+      } else if (t0 + kSeedPer <= m) {  // a caller's label array aligned to 4 bytes only
+        const unsigned* l4 = reinterpret_cast<const unsigned*>(lab + t0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[j][q] = __ldg(l4 + q);
+      } else {
+        for (int i = 0; i < kSeedPer && t0 + i < m; ++i)
+          w[j][i >> 2] |= (unsigned)__ldg(lab + t0 + i) << (8 * (i & 3));
+      }
     }
-    int pos = before + incl - cnt;
-    while (smask) {  // the seeds only, in increasing order
-      const int i = __ffs(smask) - 1;
-      smask &= smask - 1;
-      const unsigned wq = i < 8 ? (i < 4 ? w[0] : w[1]) : (i < 12 ? w[2] : w[3]);
-      const unsigned fr = (wq >> (8 * (i & 3) + 2)) & 7u;
-      const int t = (int)(t0 + i);
-      s_seed[pos] = t;
-      s_entry[pos] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
-      ++pos;
+#pragma unroll
+    for (int j = 0; j < kSeedSub; ++j) {
+      unsigned sm = 0;  // bit i: triangle t0 + i is a seed
+#pragma unroll
+      for (int i = 0; i < kSeedPer; ++i) sm |= ((w[j][i >> 2] >> (8 * (i & 3) + 5)) & 1u) << i;
+      smask[j] = sm;
+      cnt[j] = __popc(sm);
+      int x = cnt[j];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+      }
+      incl[j] = x;
+      if (lane == 31) sw[j][warp] = x;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < total; k += kBlock) {
-      seeds[base + k] = s_seed[k];
-      if (entry) entry[base + k] = s_entry[k];
+    int sub_total[kSeedSub];
+    int total = 0;
+#pragma unroll
+    for (int j = 0; j < kSeedSub; ++j) {
+      int t = 0;
+#pragma unroll
+      for (int v = 0; v < kBlock / 32; ++v) t += sw[j][v];
+      sub_total[j] = t;
+      total += t;
+    }
+    if (warp == 0) {
+      const long long ex = lookback_warp(status, bt, total, C);
+      if (lane == 0) {
+        s_base = ex;
+        if (bt == nbt - 1) C->n_seeds = ex + total;
+        // the last look-back to complete clears the status words for the next run
+        const unsigned long long done =
+            atomicAdd(reinterpret_cast<unsigned long long*>(&C->seed_done), 1ull);
+        s_clear = done == (unsigned long long)(nbt - 1);
+      }
+    }
+    __syncthreads();
+    long long base = s_base;
+#pragma unroll
+    for (int j = 0; j < kSeedSub; ++j) {
+      const long long t0 = ((bt * kSeedSub + j) * kBlock + threadIdx.x) * kSeedPer;
+      int before = 0;
+#pragma unroll
+      for (int v = 0; v < kBlock / 32; ++v) before += (v < warp) ? sw[j][v] : 0;
+      int pos = before + incl[j] - cnt[j];
+      unsigned sm = smask[j];
+      while (sm) {  // the seeds only, in increasing order
+        const int i = __ffs(sm) - 1;
+        sm &= sm - 1;
+        const unsigned wq = i < 8 ? (i < 4 ? w[j][0] : w[j][1]) : (i < 12 ? w[j][2] : w[j][3]);
+        const unsigned fr = (wq >> (8 * (i & 3) + 2)) & 7u;
+        const int t = (int)(t0 + i);
+        s_seed[pos] = t;
+        s_entry[pos] = fr ? 3 * t + (__ffs(fr) - 1) : -1 - t;
+        ++pos;
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < sub_total[j]; k += kBlock) {
+        seeds[base + k] = s_seed[k];
+        if (entry) entry[base + k] = s_entry[k];
+      }
+      base += sub_total[j];
+      __syncthreads();
+    }
+    if (s_clear) {  // every tile has finished its look-back
+      for (long long q = threadIdx.x; q < nbt; q += kBlock) status[q] = 0;
+      if (threadIdx.x == 0) C->seed_done = 0;
     }
     __syncthreads();
   }
 }
 
-cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
-                              int* seeds, int* entry, int grid, cudaStream_t s) {
+cudaError_t launch_seed_write(const uint8_t* lab, long long m, unsigned long long* status,
+                              int* seeds, int* entry, Counters* C, int grid, cudaStream_t s) {
   static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_seed_write), kBlock, 0, grid, &cap);
-  k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, tile_off, seeds, entry);
+  k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, status, seeds, entry, C);
   return cudaGetLastError();
 }
+
+long long seed_tiles(long long m) { return (m + kSeedTile - 1) / kSeedTile; }
 
 // ------------------------------------------------------------------ tile scan
 // Exclusive scan of the per-tile pairs by up to kScanBlocks blocks, none waiting

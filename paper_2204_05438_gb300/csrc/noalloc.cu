@@ -8,15 +8,15 @@
 // device heap.  The handle-based entry points allocate their scratch in
 // polylla_mesh_create, so they are closed to such callers.  This entry point takes
 // the same computation (LabelMax, the fused LabelSeed / LabelFrontier pass and the
-// ordered seed compaction) and keeps its only scratch -- the per-tile seed counts,
-// their scanned offsets and the error word -- in a file-scope __device__ array of
-// fixed size, so it allocates nothing.  The caller passes the mesh (inputs) and
+// ordered seed compaction) and keeps its only scratch -- the look-back words of
+// the seed compaction and the counters with the error word -- in a file-scope
+// __device__ array of fixed size, so it allocates nothing.  The caller passes the mesh (inputs) and
 // the label bytes, seed list and seed count (outputs).
 //
 // Limits and sharing:
 //   * at most kNoAllocMaxTri = 2^26 triangles; larger meshes are rejected with
 //     POLYLLA_ERR_INVALID_ARG before anything is launched;
-//   * the scratch array (about 2 MiB) belongs to this file's device module.  The
+//   * the scratch array (about 33 KiB) belongs to this file's device module.  The
 //     CUDA runtime loads modules lazily by default, so the array and the kernels
 //     are placed on a device by the first call on that device (its
 //     cudaGetSymbolAddress, or its first launch): that first call allocates the
@@ -27,7 +27,7 @@
 //     the process exits (or the caller resets the device);
 //   * every call on a device uses the same array and leaves its contents behind;
 //     the parts that must start at zero (the error word, the counters and the
-//     per-tile seed counts) are cleared at the start of each call, so
+//     look-back words) are cleared at the start of each call, so
 //     consecutive calls are independent, but calls that overlap on the GPU (two
 //     streams, or two host threads at once) race on it and must be serialised by
 //     the caller;
@@ -43,12 +43,13 @@ using namespace polylla;
 namespace {
 
 constexpr long long kNoAllocMaxTri = 1ll << 26;
-constexpr long long kNoAllocTiles = (kNoAllocMaxTri + kTriTile - 1) / kTriTile;
-constexpr size_t kTileBytes = sizeof(long long) * 2 * (size_t)kNoAllocTiles;
-constexpr size_t kCountersOffset = 2 * kTileBytes;
+// look-back words of the seed compaction: one per 16384-triangle tile, and one spare
+constexpr long long kNoAllocTiles = kNoAllocMaxTri / 16384 + 1;
+constexpr size_t kStatusBytes = sizeof(unsigned long long) * (size_t)kNoAllocTiles;
+constexpr size_t kCountersOffset = (kStatusBytes + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kCountersOffset + ((sizeof(Counters) + 255) / 256) * 256;
 
-// The whole scratch of this entry point: tile sums, tile offsets, counters.
+// The whole scratch of this entry point: look-back words, counters.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Device address of the scratch array on the current device.  The host-side
@@ -89,8 +90,7 @@ extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64
   unsigned char* base = nullptr;
   int sms = 0;
   if (scratch_for(dev, &base, &sms) != cudaSuccess) return POLYLLA_ERR_CUDA;
-  long long* tile_sum = reinterpret_cast<long long*>(base);
-  long long* tile_off = reinterpret_cast<long long*>(base + kTileBytes);
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(base);
   Counters* C = reinterpret_cast<Counters*>(base + kCountersOffset);
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -100,18 +100,18 @@ extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64
   M.twin = d_twin;
   M.n = n_vertices;
   M.m = n_tri;
-  // the error word, counters and tile sums start at zero
+  // the error word, counters and look-back words start at zero
+  if (seed_tiles(n_tri) + 1 > kNoAllocTiles) return POLYLLA_ERR_INVALID_ARG;
   cudaError_t e = cudaMemsetAsync(C, 0, sizeof(Counters), s);
-  const long long ntiles = (n_tri + kTriTile - 1) / kTriTile;  // counts accumulate by atomics
-  if (e == cudaSuccess) e = cudaMemsetAsync(tile_sum, 0, 2 * sizeof(long long) * (size_t)ntiles, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(seed_tiles(n_tri) + 1), s);
   if (e == cudaSuccess) e = launch_label_max(M, d_lab, C, grid_of(sms, (n_tri + 3) / 4, kBlock), s);
-  if (e == cudaSuccess) e = launch_label_class(M, d_lab, tile_sum, nullptr, C, grid_of(sms, n_tri, kTriTile), s);
+  if (e == cudaSuccess) e = launch_label_class(M, d_lab, nullptr, C, grid_of(sms, n_tri, kTriTile), s);
   if (e == cudaSuccess)
-    e = launch_scan_tiles(tile_sum, tile_off, n_tri, nullptr, n_tri, kTriTile,
-                          reinterpret_cast<long long*>(d_n_seeds), &C->scratch0, nullptr, 0, 0, C,
-                          s);
+    e = launch_seed_write(d_lab, n_tri, status, d_seeds, nullptr, C,
+                          grid_of(sms, n_tri, 16 * kTriTile), s);
   if (e == cudaSuccess)
-    e = launch_seed_write(d_lab, n_tri, tile_off, d_seeds, nullptr, grid_of(sms, n_tri, kTriTile), s);
+    e = cudaMemcpyAsync(d_n_seeds, &C->n_seeds, sizeof(long long), cudaMemcpyDeviceToDevice, s);
   int err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &C->error, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

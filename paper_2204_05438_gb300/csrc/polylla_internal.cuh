@@ -46,6 +46,9 @@ struct Counters {
   long long n_long2;      // long polygons handed from the small blocks to the large ones
   long long n_long_seq;   // long regions too large for a block, walked by one thread
   long long n_multi_seq;  // several-tip polygons with more tips than the node list holds
+  long long seed_ticket;  // tile tickets of the seed compaction's look-back
+  long long seed_done;    // its completed look-backs (the last one clears the status)
+  long long out_done;     // the output pass's completed look-backs (likewise)
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
   int error;              // first device error (polylla_status), 0 if none
@@ -197,10 +200,14 @@ inline int resident_grid(const void* kernel, int threads, size_t smem, long long
 cudaError_t launch_validate(const DevMesh& M, Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int grid,
                              cudaStream_t s);
-cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, long long* tile_sum, int* tf,
-                               Counters* C, int grid, cudaStream_t s);
-cudaError_t launch_seed_write(const uint8_t* lab, long long m, const long long* tile_off,
-                              int* seeds, int* entry, int grid, cudaStream_t s);
+cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, int* tf, Counters* C, int grid,
+                               cudaStream_t s);
+// The ascending seed list (and entries, if non-null) and C->n_seeds in one pass:
+// look-back over `status` (seed_tiles(m) words, zero at the first use; left zero)
+// with tickets from C->seed_ticket (zero at the start).
+cudaError_t launch_seed_write(const uint8_t* lab, long long m, unsigned long long* status,
+                              int* seeds, int* entry, Counters* C, int grid, cudaStream_t s);
+long long seed_tiles(long long m);
 // Exclusive scan of per-tile pairs.  Tile count = ceil(n / tile) with n = *n_dev if
 // n_dev, else n_host.  Totals go to *tot0, *tot1.  end_mode 1: end[n] = total0;
 // end_mode 2: end[total0] = total1 (index checked against end_cap).
@@ -247,12 +254,16 @@ struct LongList {
 // lab: the label bytes (their frontier bits select the half-edges to turn)
 cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
                         Counters* C, int grid, cudaStream_t s);
-// One thread per seed: walk (<= kWalkCap) and, if `repair`, split the polygon.
-// cap: polygons longer than cap (16, 32, 48 or 64) go to the long-polygon blocks.
+// One thread per seed: walk (<= kWalkCap) and, if `repair`, list polygons with
+// tips.  cap: polygons longer than cap (16, 32, 48 or 64) go to the long-polygon
+// blocks; with tips_to_long > 0 (small meshes), so do polygons with that many tips
+// or more when `repair` (the block splits their tips in parallel; one thread would
+// split them one after another).
+constexpr long long kSmallMeshTri = 1ll << 16;  // meshes below this: tips_to_long = 3
 cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
                         const PolyArrays& P, const Pool& pool, const LongList& Lg,
                         const LongList& D1, const LongList& Dm, int cap, int repair,
-                        Counters* C, int grid, cudaStream_t s);
+                        int tips_to_long, Counters* C, int grid, cudaStream_t s);
 // One thread per polygon with one tip / with several tips (listed by k_walk).
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
@@ -268,8 +279,9 @@ cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seed
                         const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                         const LongList& Lg, const LongList& Lg2, int* loc, int* vstamp, int epoch,
                         int repair, int mode, Counters* C, int sms, cudaStream_t s);
-// Output: the CSR offsets (a look-back scan over `status`, zeroed, one word per
-// 256-polygon tile) and the copy; also C->n_poly, C->n_vtx and off[n_poly].
+// Output: the CSR offsets (a look-back scan over `status`, one word per
+// 1024-polygon tile, zero at the first use and left zero) and the copy; also
+// C->n_poly, C->n_vtx and off[n_poly].
 // obase (nullable): per traversal polygon, the index of its first output polygon.
 cudaError_t launch_final_write(const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                                unsigned long long* status, long long* off, int* vtx,

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
                                                        const int* __restrict__ succ, PolyArrays P,
                                                        Pool pool, LongList Lg, LongList D1,
                                                        LongList Dm, int cap, int repair,
-                                                       Counters* C) {
+                                                       int tips_to_long, Counters* C) {
   // staging transposed (word q of thread x at q * blockDim + x): the lanes of a
   // warp, writing the same position in lockstep, hit 32 different banks
   extern __shared__ int sbuf[];
@@ -225,6 +225,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
         } while (h != e && len < cap);
         closed = ok && h == e;
         is_long = ok && !closed;
+        // several tips on a small mesh: the block kernel splits them in parallel
+        if (closed && repair && tips_to_long > 0 && ntips >= tips_to_long) {
+          closed = false;
+          is_long = true;
+        }
         if (!ok) set_error(C, POLYLLA_ERR_LIMIT, 52);
         start = (int)(best & 0xffffffffu);
       }
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
 cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
                         const PolyArrays& P, const Pool& pool, const LongList& Lg,
                         const LongList& D1, const LongList& Dm, int cap, int repair,
-                        Counters* C, int grid, cudaStream_t s) {
+                        int tips_to_long, Counters* C, int grid, cudaStream_t s) {
   if (cap < 16 || cap > kWalkCap || cap % 16) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int) * (size_t)kWalkThreads * cap;
   static std::atomic<bool> attr{false};
@@ -301,7 +306,7 @@ cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* 
   grid = resident_grid(reinterpret_cast<const void*>(k_walk), kWalkThreads, smem, grid,
                        &resident[cap / 16]);
   k_walk<<<grid, kWalkThreads, smem, s>>>(M, tf, entry, succ, P, pool, Lg, D1, Dm, cap, repair,
-                                          C);
+                                          tips_to_long, C);
   return cudaGetLastError();
 }
 

@@ -41,8 +41,10 @@ def test_region_too_large_for_a_block_is_walked_by_one_thread():
 
 
 def test_polygon_with_more_tips_than_the_node_list_is_split_by_rewalking():
-    """Three 56-vertex polygons with 10 tips each (the node list holds 8 splits)."""
-    mesh = disjoint_union([tip_hub(), tip_hub(), meshgen.generate("uniform", 2000, 1 << 22, 32),
+    """Three 56-vertex polygons with 10 tips each (the node list holds 8 splits), in a
+    mesh of more than 2^16 triangles (smaller meshes give such polygons to the
+    block kernel)."""
+    mesh = disjoint_union([tip_hub(), tip_hub(), meshgen.generate("uniform", 40_000, 1 << 22, 32),
                            tip_hub()])
     g = assert_parity(mesh)
     st = g["stats"]
@@ -51,13 +53,25 @@ def test_polygon_with_more_tips_than_the_node_list_is_split_by_rewalking():
     assert st["n_splits"] >= 30
 
 
+def test_small_mesh_gives_several_tip_polygons_to_the_block_kernel():
+    """Below 2^16 triangles, polygons with three or more tips are split by one thread
+    block each (the tips in parallel) instead of one thread; the result is the same."""
+    mesh = disjoint_union([tip_hub(), meshgen.generate("gmm", 3000, 1 << 22, 34), tip_hub()])
+    g = assert_parity(mesh)
+    st = g["stats"]
+    assert st["n_multi_seq"] == 0
+    assert st["n_long"] >= 2
+    assert st["n_splits"] >= 20
+
+
 def test_batch_schedules_hand_long_regions_to_large_blocks():
     """Wheels of 100, 200, 1000 and 5000 triangles and a ten-tip hub in one batch:
     under the schedules that try one-warp (128 members) or small (512) blocks first,
     the larger regions are handed to the large blocks, and the 5000-triangle one on
     to the one-thread walk; every schedule gives every mesh the oracle's polygons."""
     meshes = [spiral_wheel(100), spiral_wheel(200), meshgen.generate("gmm", 1500, 1 << 22, 33),
-              spiral_wheel(1000), tip_hub(), spiral_wheel(5000)]
+              spiral_wheel(1000), tip_hub(), spiral_wheel(5000),
+              meshgen.generate("uniform", 40_000, 1 << 22, 35)]  # > 2^16 triangles in all
     refs = [oracle.run(m) for m in meshes]
     cat = meshgen.concat(meshes)
     B = pg.batch_from_numpy(cat)
