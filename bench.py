@@ -45,16 +45,16 @@ FALLBACK_HBM_GBS = 6800.0
 # on the gmm16-10m workload, keyed by the hash of the device code they were taken
 # with (source_hash); reported as null once that code changes.
 NCU_TRAFFIC = {
-    "sources": "50c98666d13065ef",
-    # one ncu --set full capture on gmm16-5m (9,999,947 triangles), scaled x2.0000 by
-    # triangle count to a gmm16-10m launch
-    "bytes": {"walk": int((311.269888 + 62.923776) * 1e6 * 19999948 / 9999947),
-              "succ": int((232.308736 + 105.336576) * 1e6 * 19999948 / 9999947),
-              "out_write": int((90.196480 + 28.728832) * 1e6 * 19999948 / 9999947),
-              "label_class": int((130.262528 + 80.321792) * 1e6 * 19999948 / 9999947),
-              "label_max": int((200.069120 + 8.648192) * 1e6 * 19999948 / 9999947),
-              "seed_write": int((10.166016 + 0.000000) * 1e6 * 19999948 / 9999947),
-              "repair_one": int((134.347008 + 10.521856) * 1e6 * 19999948 / 9999947)},
+    "sources": "fc5541348bfaf6f8",
+    # one ncu --set full capture per kernel on gmm16-5m (9,999,947 triangles),
+    # scaled x2.0000 by triangle count to a gmm16-10m launch
+    "bytes": {"walk": int((311.339520 + 63.277824) * 1e6 * 19999948 / 9999947),
+              "succ": int((232.428800 + 105.648128) * 1e6 * 19999948 / 9999947),
+              "out_write": int((90.242560 + 27.788800) * 1e6 * 19999948 / 9999947),
+              "label_class": int((130.077184 + 80.088576) * 1e6 * 19999948 / 9999947),
+              "label_max": int((200.065024 + 9.052416) * 1e6 * 19999948 / 9999947),
+              "seed_write": int((10.045952 + 0.000768) * 1e6 * 19999948 / 9999947),
+              "repair_one": int((134.412032 + 11.003648) * 1e6 * 19999948 / 9999947)},
 }
 
 
