@@ -108,6 +108,9 @@ typedef struct {
   int64_t n_multi_tip;    /* polygons with several tips, split in shared memory */
   int64_t n_multi_seq;    /* of those, polygons with more tips than the shared node
                              list holds, split by re-walking */
+  int64_t n_one_chase;    /* one-tip polygons whose pieces could not be cut out of the
+                             traversal's vertex sequence (a repeated vertex), split by
+                             chasing the successors */
 } polylla_stats;
 
 /*

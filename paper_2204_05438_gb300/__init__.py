@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n_seeds", "n_poly_trav", "n_vtx_trav", "n_tip_polygons", "n_tips", "n_splits",
         "n_poly", "n_vtx", "n_long", "n_long_handoff", "n_long_seq", "n_one_tip", "n_multi_tip",
-        "n_multi_seq")]
+        "n_multi_seq", "n_one_chase")]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

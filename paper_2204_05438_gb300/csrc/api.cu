@@ -363,7 +363,7 @@ polylla_status do_label(polylla_mesh* h, cudaStream_t s) {
   POLY_TRY(launch(h, "label_max", s, [&] { return launch_label_max(M, h->lab, h->C, g1, s); }));
   const int g2 = grid_for(h, M.m, kTriTile);
   POLY_TRY(launch(h, "label_class", s, [&] {
-    return launch_label_class(M, h->lab, h->tf, h->C, g2, s);
+    return launch_label_class(M, h->lab, h->tf, h->C, g2, s, !h->timing);
   }));
   h->phase = kLabeled;
   h->lepp_valid = false;
@@ -376,7 +376,8 @@ polylla_status do_seeds(polylla_mesh* h, cudaStream_t s) {
   const DevMesh& M = h->M;
   const int g = grid_for(h, M.m, 16 * kTriTile);
   POLY_TRY(launch(h, "seed_write", s, [&] {
-    return launch_seed_write(h->lab, M.m, h->seed_status, h->seeds, h->entry, h->C, g, s);
+    return launch_seed_write(h->lab, M.m, h->seed_status, h->seeds, h->entry, h->C, g, s,
+                             !h->timing && h->phase == kLabeled);
   }));
   h->phase = kSeeded;
   return POLYLLA_OK;
@@ -389,21 +390,27 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   const DevMesh& M = h->M;
   // counters of this pass start at zero: right after the seeds they are (the label
   // phase cleared them); after a traversal pass they are cleared here
+  // the kernel chain continues without a gap where the previous operation on the
+  // stream is its predecessor kernel: succ right after the seeds, the walk right
+  // after succ (not in timing mode, where events sit between the kernels)
+  const bool pdl = !h->timing && h->phase == kSeeded;
+  const bool succ_runs = repair == 0 || h->phase < kTraversed;
   if (h->phase != kSeeded) {
     const size_t first = offsetof(Counters, n_vtx_trav);
     const size_t last = offsetof(Counters, seed_ticket);
     POLY_TRY(cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(h->C) + first, 0, last - first, s)));
   }
-  if (repair == 0 || h->phase < kTraversed) {
+  if (succ_runs) {
     const int gt = grid_for(h, M.m, kBlock);
     POLY_TRY(launch(h, "succ", s, [&] {
-      return launch_succ(M, h->lab, h->tf, h->succ, h->C, gt, s);
+      return launch_succ(M, h->lab, h->tf, h->succ, h->C, gt, s, pdl);
     }));
   }
   const int gw = grid_for(h, M.m, 4 * 256);
   POLY_TRY(launch(h, "walk", s, [&] {
     return launch_walk(M, h->tf, h->entry, h->succ, h->P, h->pool, h->Lg, h->Dl, h->Dm,
-                       h->walk_cap, repair, M.m < kSmallMeshTri ? 3 : 0, h->C, gw, s);
+                       h->walk_cap, repair, M.m < kSmallMeshTri ? 3 : 0, h->C, gw, s,
+                       !h->timing && succ_runs);
   }));
   // repair_one (this stream), repair_multi and long (side streams) at once
   const bool fork = !h->timing && h->overlap;
@@ -929,6 +936,7 @@ polylla_status polylla_get_stats(polylla_mesh_t h, polylla_stats* out) {
     out->n_one_tip = c.n_defer;
     out->n_multi_tip = c.n_multi;
     out->n_multi_seq = c.n_multi_seq;
+    out->n_one_chase = c.n_one_chase;
   }
   return POLYLLA_OK;
 }

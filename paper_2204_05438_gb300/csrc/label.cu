@@ -91,6 +91,7 @@ __device__ __forceinline__ long long sqdist(longlong2 p, longlong2 q) {
 // The twin array is read only for triangles whose longest length is tied.
 __global__ void __launch_bounds__(kBlock, 6) k_label_max(DevMesh M, uint8_t* __restrict__ lab,
                                                       Counters* C) {
+  pdl_launch_dependents();
   const long long m = M.m, n = M.n;
   const long long ngroups = (m + 3) / 4;
   const longlong2* __restrict__ xy2 = reinterpret_cast<const longlong2*>(M.xy);
@@ -166,6 +167,8 @@ cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int gr
 // triangles are independent.
 __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* lab,
                                                            int* __restrict__ tf, Counters* C) {
+  pdl_wait();  // the Max array
+  pdl_launch_dependents();
   const long long m = M.m;
   const long long H = 3 * m;
   const long long ntiles = (m + kTriTile - 1) / kTriTile;
@@ -234,11 +237,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_label_class(DevMesh M, uint8_t* l
 }
 
 cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, int* tf, Counters* C, int grid,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool pdl) {
   static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_label_class), kBlock, 0, grid, &cap);
-  k_label_class<<<grid, kBlock, 0, s>>>(M, lab, tf, C);
-  return cudaGetLastError();
+  return launch_chain(k_label_class, grid, kBlock, 0, s, pdl, M, lab, tf, C);
 }
 
 // ------------------------------------------------------------------ seed compaction
@@ -268,6 +270,8 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
   __shared__ int s_seed[kSeedSpan], s_entry[kSeedSpan];
   __shared__ long long s_tile, s_base;
   __shared__ int s_clear;
+  pdl_wait();  // the label bytes
+  pdl_launch_dependents();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long nbt = (m + kSeedTile - 1) / kSeedTile;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(lab) & 15u) == 0;
@@ -375,11 +379,11 @@ __global__ void __launch_bounds__(kBlock) k_seed_write(const uint8_t* __restrict
 }
 
 cudaError_t launch_seed_write(const uint8_t* lab, long long m, unsigned long long* status,
-                              int* seeds, int* entry, Counters* C, int grid, cudaStream_t s) {
+                              int* seeds, int* entry, Counters* C, int grid, cudaStream_t s,
+                              bool pdl) {
   static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_seed_write), kBlock, 0, grid, &cap);
-  k_seed_write<<<grid, kBlock, 0, s>>>(lab, m, status, seeds, entry, C);
-  return cudaGetLastError();
+  return launch_chain(k_seed_write, grid, kBlock, 0, s, pdl, lab, m, status, seeds, entry, C);
 }
 
 long long seed_tiles(long long m) { return (m + kSeedTile - 1) / kSeedTile; }

@@ -5,10 +5,12 @@
 // load at a time would make each of them the critical path of the run.  A block:
 //
 //   1. collects the region's frontier half-edges by a breadth-first search over
-//      its triangles across non-frontier edges (tf words), with the visited set in
-//      a shared-memory hash table.  Every triangle reaches its seed through its
-//      longest-edge links, so the search from the seed ends after at most
-//      (longest-edge propagation depth + 1) levels;
+//      its triangles across non-frontier edges (tf words).  The non-frontier edges
+//      form a tree (each triangle hangs from the neighbour across its longest
+//      edge, Section 3.2.1's labels: a frontier edge is the longest edge of
+//      neither of its triangles), so the search goes down it
+//      from the seed without a visited set and ends after (longest-edge
+//      propagation depth + 1) levels;
 //   2. maps each half-edge's successor to a member index, finds the canonical
 //      start by a block reduction;
 //   3. without reparation (or tips): ranks the cycle from its start by pointer
@@ -23,7 +25,8 @@
 //      canonical start; a piece is named by its smallest split half-edge), ranks
 //      them, orders them as the recursive splitting emits them (first the chord of
 //      the smallest tip, the tip->x side first: merging pieces across chords in
-//      decreasing tip order builds that tree) and writes them to the pool.
+//      decreasing tip order builds that tree, on one thread; the rest is parallel)
+//      and writes them to the pool.
 //
 // A region too large for the shared-memory budget is handled by one thread of the
 // block with the sequential code (long_fallback).
@@ -31,13 +34,19 @@
 
 namespace polylla {
 
-// Two sizes of the block: a large one (4096 members, 4096 triangles, 512 threads,
-// about 180 KB of shared memory: one block per SM) for any region, and a small
-// one (512 members, 512 triangles, 128 threads, about 22 KB: several blocks per
-// SM) that hands a region it cannot hold to the large one.
+// Three sizes of the block: a large one (4096 members, 4096 triangles, 512 threads,
+// about 180 KB of shared memory: one block per SM) for any region; a medium one
+// (2048 members and triangles, 256 threads, about 90 KB) that leaves room on its SM
+// for the split kernels running beside it; and a small one (512 members, 512
+// triangles, 128 threads, about 22 KB: several blocks per SM).  The medium and
+// small blocks hand a region they cannot hold to the large one.
 constexpr int kLongThreads = 512;
 constexpr int kLM = 4096;  // members of one long polygon (with its split half-edges)
 constexpr int kLT = 4096;  // BFS queue: triangles of one long region
+constexpr int kMedThreads = 256;
+constexpr int kMedLM = 2048;
+constexpr int kMedLT = 2048;
+constexpr int kLargeAfterMed = 16;  // large blocks behind the medium ones (rare regions)
 constexpr int kSmallThreads = 128;
 constexpr int kSmallLM = 512;
 constexpr int kSmallLT = 512;
@@ -46,23 +55,6 @@ constexpr int kWarpLT = 128;
 
 template <int LM, int LT>
 constexpr int long_smem_ints() { return LT + 10 * LM; }
-
-// Insert triangle t into the block's visited table of 2 * LM slots (open
-// addressing, -1 = empty).  Returns 1 if t was new, 0 if it was there, -1 if the
-// table is full.
-template <int LM>
-__device__ __forceinline__ int visit_insert(int* tab, int t) {
-  constexpr int kSlots = 2 * LM;
-  static_assert((kSlots & (kSlots - 1)) == 0, "a power of two");
-  unsigned slot = ((unsigned)t * 2654435761u) & (kSlots - 1);
-  for (int probe = 0; probe < kSlots; ++probe) {
-    const int old = atomicCAS(tab + slot, -1, t);
-    if (old == -1) return 1;
-    if (old == t) return 0;
-    slot = (slot + 1) & (kSlots - 1);
-  }
-  return -1;
-}
 
 __device__ void block_min_key(unsigned long long key, int idx, unsigned long long* s_key,
                               int* s_idx, unsigned long long* out_key, int* out_idx) {
@@ -102,6 +94,37 @@ __device__ void block_min_key(unsigned long long key, int idx, unsigned long lon
   *out_key = s_key[0];
   *out_idx = s_idx[0];
   __syncthreads();
+}
+
+// Exclusive prefix sum of v over the block in thread order; *total gets the sum.
+// Every thread of the block calls it; s_wsum holds 33 ints.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* s_wsum, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+  int incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = lane < nw ? s_wsum[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += y;
+    }
+    if (lane < nw) s_wsum[lane] = wi - w;
+    if (lane == 31) s_wsum[32] = wi;
+  }
+  __syncthreads();
+  const int r = s_wsum[warp] + incl - v;
+  *total = s_wsum[32];
+  __syncthreads();
+  return r;
 }
 
 // Pointer jumping on successor lists (nx: successor, or -1 at a list's end):
@@ -222,7 +245,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
                                                   Counters* C) {
   constexpr int kLM = LM;
   constexpr int kLT = LT;
-  constexpr int kHashSlots = 2 * LM;
   extern __shared__ int smem[];
   int* RQ = smem;       // BFS queue; later the chord list and ordering counts
   int* mem = RQ + kLT;  // members
@@ -235,9 +257,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
   int* const R6 = mem + 7 * kLM;
   int* const R7 = mem + 8 * kLM;
   int* const R8 = mem + 9 * kLM;
-  __shared__ int s_head, s_tail, s_nm, s_over, s_nt, s_ns, s_fail;
+  __shared__ int s_cnt[3], s_ovf[3], s_nm, s_nt, s_ns, s_fail;
   __shared__ unsigned long long s_key[32];
   __shared__ int s_idx[32];
+  __shared__ int s_wsum[33];
   __shared__ long long s_base, s_fbase;
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
@@ -245,55 +268,65 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
   for (long long j = blockIdx.x; j < nl; j += gridDim.x) {
     const long long i = Lg.poly[j];
     const int t0 = seeds[i];
-    // ---- 1. breadth-first search of the region
-    int* vis = R0;  // R0..R1: the visited table
-    for (int q = threadIdx.x; q < kHashSlots; q += blockDim.x) vis[q] = -1;
-    __syncthreads();
+    // ---- 1. the region's triangles, by a breadth-first search down its
+    //         longest-edge tree: every non-frontier edge is the longest edge of one
+    //         of its triangles, and every triangle but the seed's terminal pair hangs
+    //         from the neighbour across its longest edge.  So from a triangle t the
+    //         search crosses the non-frontier edges other than t's longest (from the
+    //         seed, all of them: its longest edge leads to its terminal partner), and
+    //         meets each triangle of the region once, without a visited set.  One
+    //         barrier per level: the triangles found in level i go after the level's
+    //         range, counted by s_cnt[i % 3] (overflow / error flag s_ovf[i % 3]);
+    //         the count and flag of level i - 2 are cleared during level i, when
+    //         every thread has read them.
     if (threadIdx.x == 0) {
-      s_head = 0;
-      s_tail = 1;
+      for (int c = 0; c < 3; ++c) {
+        s_cnt[c] = 0;
+        s_ovf[c] = 0;
+      }
       s_nm = 0;
-      s_over = 0;
       RQ[0] = t0;
-      visit_insert<LM>(vis, t0);
     }
     __syncthreads();
-    for (;;) {
-      const int lo = s_head, hi = s_tail, over = s_over;
-      __syncthreads();
-      if (lo >= hi || over) break;
+    int ovf = 0;
+    for (int lvl = 0, lo = 0, hi = 1;; ++lvl) {
+      const int c = lvl % 3;
       for (int q = lo + threadIdx.x; q < hi; q += blockDim.x) {
         const int t = RQ[q];
+        int x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = tf[3 * t + k];
+        const int up = (t == t0) ? -1 : (int)(lab[t] & 3u);  // the longest edge
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const int x = tf[3 * t + k];
-          if (x < 0) {
+          if (x[k] < 0) {
             const int mi = atomicAdd(&s_nm, 1);
             if (mi < kLM) mem[mi] = 3 * t + k;
-            else s_over = 1;
-          } else if (x >= H) {
-            s_over = 2;
-          } else {
-            const int nb = x / 3;
-            const int ins = visit_insert<LM>(vis, nb);
-            if (ins > 0) {
-              const int p = atomicAdd(&s_tail, 1);
-              if (p < kLT) RQ[p] = nb;
-              else s_over = 1;
-            } else if (ins < 0) {
-              s_over = 1;
-            }
+            else s_ovf[c] = 1;
+          } else if (x[k] >= H) {
+            s_ovf[c] = 2;
+          } else if (k != up) {
+            const int p = hi + atomicAdd(&s_cnt[c], 1);
+            if (p < kLT) RQ[p] = x[k] / 3;
+            else s_ovf[c] = 1;
           }
         }
       }
+      if (threadIdx.x == 0) {
+        s_cnt[(lvl + 1) % 3] = 0;
+        s_ovf[(lvl + 1) % 3] = 0;
+      }
       __syncthreads();
-      if (threadIdx.x == 0) s_head = hi;
-      __syncthreads();
+      ovf = s_ovf[c];
+      const int found = s_cnt[c];
+      if (ovf || found == 0) break;
+      lo = hi;
+      hi += found;
     }
     const int L = s_nm;
-    if (s_over) {
+    if (ovf) {
       if (threadIdx.x == 0) {
-        if (s_over == 2) {
+        if (ovf == 2) {
           set_error(C, POLYLLA_ERR_LIMIT, 106);
         } else if (over.poly) {  // too large for this block: the large blocks take it
           const long long q =
@@ -544,85 +577,96 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
     __syncthreads();
     const int* dist = list_rank(R0, R1, R2, R3, N);
     int* pos = (dist == R2) ? R3 : R2;  // the free one of the ranking buffers
-    int* nodeof = R0;                        // piece name - L -> node
-    // ---- 4f. order of the pieces, pool and piece records (one thread)
-    if (threadIdx.x == 0) {
-      const int W = 2 * ns + 1;
-      int* node_name = R1;
-      int* uf = R4;
-      int* left = R5;
-      int* right = R6;
-      int* cnt = RQ;
-      int npieces = 0;
-      bool bad = false;
-      for (int q = 0; q < 2 * ns; ++q) nodeof[q] = -1;
-      for (int q = 0; q < 2 * ns && !bad; ++q) {
+    int* nodeof = R0;                   // piece name - L -> leaf
+    int* node_name = R1;
+    int* uf = R4;
+    int* left = R5;
+    int* right = R6;
+    int* cnt = RQ;
+    // ---- 4f. the pieces' order.  Leaves: the pieces in increasing name order
+    //          (member L + q names its piece when B[A[L + q]] == L + q; a block
+    //          scan numbers them).  One thread merges the pieces across the chords
+    //          in decreasing tip order into the chord tree and takes the leaves'
+    //          positions from its subtree sizes; warp 0 turns the lengths in that
+    //          order into offsets.
+    int npieces = 0;
+    {
+      const int per = (2 * ns + (int)blockDim.x - 1) / (int)blockDim.x;
+      const int q0 = (int)threadIdx.x * per;
+      const int q1 = min(q0 + per, 2 * ns);
+      int mine = 0;
+      for (int q = q0; q < q1; ++q) {
         const int name = B[A[L + q]];
-        if (name < L || name >= N) {
+        if (name < L || name >= N) s_fail = 1;
+        mine += name == L + q;
+      }
+      int id = block_exclusive_scan(mine, s_wsum, &npieces);
+      for (int q = q0; q < q1; ++q) {
+        if (B[A[L + q]] == L + q) {
+          nodeof[q] = id;
+          node_name[id++] = L + q;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_fail || npieces != ns + 1) {
+      if (threadIdx.x == 0) set_error(C, POLYLLA_ERR_LIMIT, 110);
+      __syncthreads();
+      continue;
+    }
+    for (int v = threadIdx.x; v < npieces; v += blockDim.x) {
+      uf[v] = v;
+      pos[v] = v;
+    }
+    for (int q = threadIdx.x; q < ns; q += blockDim.x) {  // the leaves on either side of chord q
+      cnt[2 * q] = nodeof[B[A[L + 2 * q]] - L];
+      cnt[2 * q + 1] = nodeof[B[A[L + 2 * q + 1]] - L];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const long long base = (long long)atomicAdd(
+          reinterpret_cast<unsigned long long*>(&C->pool_alloc), (unsigned long long)N);
+      const long long fb = (long long)atomicAdd(
+          reinterpret_cast<unsigned long long*>(&C->fslot_alloc), (unsigned long long)npieces);
+      const int W = 2 * ns + 1;
+      int nodes = npieces;
+      bool bad = false;
+      for (int q = ns - 1; q >= 0; --q) {  // decreasing tip vertex
+        int ra = cnt[2 * q];
+        int rb = cnt[2 * q + 1];
+        while (uf[ra] != ra) ra = uf[ra] = uf[uf[ra]];
+        while (uf[rb] != rb) rb = uf[rb] = uf[uf[rb]];
+        if (ra == rb || nodes >= W) {
           bad = true;
           break;
         }
-        if (nodeof[name - L] < 0) {
-          nodeof[name - L] = npieces;
-          node_name[npieces++] = name;
-        }
+        const int u = nodes++;
+        left[u] = pos[ra];
+        right[u] = pos[rb];
+        uf[rb] = ra;
+        pos[ra] = u;
       }
-      if (bad || npieces != ns + 1) {
-        set_error(C, POLYLLA_ERR_LIMIT, 110);
+      if (bad) {
+        set_error(C, POLYLLA_ERR_LIMIT, 111);
         s_fail = 1;
       } else {
-        for (int v = 0; v < npieces; ++v) {
-          uf[v] = v;
-          pos[v] = v;
+        for (int v = 0; v < npieces; ++v) cnt[v] = 1;  // subtree sizes (in leaves)
+        for (int u = npieces; u < nodes; ++u) cnt[u] = cnt[left[u]] + cnt[right[u]];
+        pos[nodes - 1] = 0;
+        for (int u = nodes - 1; u >= npieces; --u) {
+          pos[left[u]] = pos[u];
+          pos[right[u]] = pos[u] + cnt[left[u]];
         }
-        int nodes = npieces;
-        for (int q = ns - 1; q >= 0 && !bad; --q) {  // decreasing tip vertex
-          int ra = nodeof[B[A[L + 2 * q]] - L];
-          int rb = nodeof[B[A[L + 2 * q + 1]] - L];
-          while (uf[ra] != ra) ra = uf[ra] = uf[uf[ra]];
-          while (uf[rb] != rb) rb = uf[rb] = uf[uf[rb]];
-          if (ra == rb || nodes >= W) {
-            bad = true;
-            break;
-          }
-          const int u = nodes++;
-          left[u] = pos[ra];
-          right[u] = pos[rb];
-          uf[rb] = ra;
-          pos[ra] = u;
-        }
-        if (bad) {
-          set_error(C, POLYLLA_ERR_LIMIT, 111);
+        if (base + N > pool.cap || fb + npieces > F.cap) {
+          set_error(C, POLYLLA_ERR_LIMIT, 112);
           s_fail = 1;
         } else {
-          for (int v = 0; v < npieces; ++v) cnt[v] = 1;
-          for (int u = npieces; u < nodes; ++u) cnt[u] = cnt[left[u]] + cnt[right[u]];
-          pos[nodes - 1] = 0;
-          for (int u = nodes - 1; u >= npieces; --u) {
-            pos[left[u]] = pos[u];
-            pos[right[u]] = pos[u] + cnt[left[u]];
-          }
-          const long long base = (long long)atomicAdd(
-              reinterpret_cast<unsigned long long*>(&C->pool_alloc), (unsigned long long)N);
-          const long long fb = (long long)atomicAdd(
-              reinterpret_cast<unsigned long long*>(&C->fslot_alloc), (unsigned long long)npieces);
-          if (base + N > pool.cap || fb + npieces > F.cap) {
-            set_error(C, POLYLLA_ERR_LIMIT, 112);
-            s_fail = 1;
-          } else {
-            for (int v = 0; v < npieces; ++v) cnt[pos[v]] = dist[A[node_name[v]]] + 1;
-            long long acc = base;
-            for (int p = 0; p < npieces; ++p) {
-              F.pos[fb + p] = acc;
-              F.len[fb + p] = cnt[p];
-              acc += cnt[p];
-            }
-            s_fbase = fb;
-            P.pcnt[i] = npieces;
-            P.pbase[i] = (int)fb;
-            P.flen[i] = N;
-            atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)ns);
-          }
+          s_base = base;
+          s_fbase = fb;
+          P.pcnt[i] = npieces;
+          P.pbase[i] = (int)fb;
+          P.flen[i] = N;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)ns);
         }
       }
     }
@@ -631,12 +675,37 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
       __syncthreads();
       continue;
     }
-    // ---- 4g. members to the pool: piece position + rank from the piece's start
-    const long long fb = s_fbase;
+    for (int v = threadIdx.x; v < npieces; v += blockDim.x)  // lengths in output order
+      cnt[pos[v]] = dist[A[node_name[v]]] + 1;
+    __syncthreads();
+    if (threadIdx.x < 32) {  // offsets and piece records
+      const int lane = threadIdx.x;
+      const long long base = s_base, fb = s_fbase;
+      int acc = 0;
+      for (int p0 = 0; p0 < npieces; p0 += 32) {
+        const int p = p0 + lane;
+        const int l = p < npieces ? cnt[p] : 0;
+        int incl = l;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        if (p < npieces) {
+          cnt[p] = acc + incl - l;
+          F.pos[fb + p] = base + acc + incl - l;
+          F.len[fb + p] = l;
+        }
+        acc += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncthreads();
+    // ---- 4g. members to the pool: piece offset + rank from the piece's start
+    const long long base = s_base;
     for (int a = threadIdx.x; a < N; a += blockDim.x) {
       const int s0 = A[a];
       const int node = nodeof[B[s0] - L];
-      pool.v[F.pos[fb + pos[node]] + (dist[s0] - dist[a])] = M.tri[mem[a]];
+      pool.v[base + cnt[pos[node]] + (dist[s0] - dist[a])] = M.tri[mem[a]];
     }
     __syncthreads();
   }
@@ -673,6 +742,15 @@ cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seed
     return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg,
                                                  &C->n_long, none, nullptr, loc, vstamp, epoch,
                                                  repair, C, sms, s);
+  if (mode == 3) {  // medium blocks, then a few large ones for what they hand over
+    cudaError_t e = launch_long_t<kMedThreads, kMedLM, kMedLT>(
+        M, lab, tf, seeds, succ, P, F, pool, Lg, &C->n_long, Lg2, &C->n_long2, loc, vstamp, epoch,
+        repair, C, sms, s);
+    if (e != cudaSuccess) return e;
+    return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg2,
+                                                 &C->n_long2, none, nullptr, loc, vstamp, epoch,
+                                                 repair, C, kLargeAfterMed, s);
+  }
   // small blocks (mode 1) or one warp per polygon (mode 2) first; the regions
   // they cannot hold, in large blocks
   cudaError_t e =

@@ -106,10 +106,11 @@ extern "C" polylla_status polylla_label_seeds_noalloc(const int64_t* d_xy, int64
   if (e == cudaSuccess)
     e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(seed_tiles(n_tri) + 1), s);
   if (e == cudaSuccess) e = launch_label_max(M, d_lab, C, grid_of(sms, (n_tri + 3) / 4, kBlock), s);
-  if (e == cudaSuccess) e = launch_label_class(M, d_lab, nullptr, C, grid_of(sms, n_tri, kTriTile), s);
+  if (e == cudaSuccess)
+    e = launch_label_class(M, d_lab, nullptr, C, grid_of(sms, n_tri, kTriTile), s, true);
   if (e == cudaSuccess)
     e = launch_seed_write(d_lab, n_tri, status, d_seeds, nullptr, C,
-                          grid_of(sms, n_tri, 16 * kTriTile), s);
+                          grid_of(sms, n_tri, 16 * kTriTile), s, true);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_n_seeds, &C->n_seeds, sizeof(long long), cudaMemcpyDeviceToDevice, s);
   int err = 0;

@@ -46,6 +46,7 @@ struct Counters {
   long long n_long2;      // long polygons handed from the small blocks to the large ones
   long long n_long_seq;   // long regions too large for a block, walked by one thread
   long long n_multi_seq;  // several-tip polygons with more tips than the node list holds
+  long long n_one_chase;  // one-tip polygons split by chasing (a repeated vertex)
   long long seed_ticket;  // tile tickets of the seed compaction's look-back
   long long seed_done;    // its completed look-backs (the last one clears the status)
   long long out_done;     // the output pass's completed look-backs (likewise)
@@ -168,6 +169,36 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return tot;
 }
 
+// ---------------------------------------------- programmatic dependent launch
+// The kernels of the chain label_max -> label_class -> seed_write -> succ -> walk
+// run back to back on one stream.  A chain kernel may be launched with
+// programmatic stream serialization (launch_chain, pdl = true) when the previous
+// operation on the stream is a kernel: its launch is then processed while the
+// previous kernel finishes, instead of after.  Every chain kernel waits
+// (pdl_wait) before it touches anything earlier work wrote -- a no-op when it was
+// launched normally -- and lets its own dependent launch (pdl_launch_dependents)
+// once all of its blocks have started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chain(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                         bool pdl, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 // ----------------------------------------------------------------- grid sizing
 // Grid-stride kernels launch at most one full wave: the blocks that fit on all
 // SMs at once (from the occupancy calculator, cached per kernel in *cache),
@@ -200,13 +231,16 @@ inline int resident_grid(const void* kernel, int threads, size_t smem, long long
 cudaError_t launch_validate(const DevMesh& M, Counters* C, int grid, cudaStream_t s);
 cudaError_t launch_label_max(const DevMesh& M, uint8_t* lab, Counters* C, int grid,
                              cudaStream_t s);
+// pdl: launch with programmatic stream serialization (the previous operation on
+// the stream is a kernel)
 cudaError_t launch_label_class(const DevMesh& M, uint8_t* lab, int* tf, Counters* C, int grid,
-                               cudaStream_t s);
+                               cudaStream_t s, bool pdl);
 // The ascending seed list (and entries, if non-null) and C->n_seeds in one pass:
 // look-back over `status` (seed_tiles(m) words, zero at the first use; left zero)
 // with tickets from C->seed_ticket (zero at the start).
 cudaError_t launch_seed_write(const uint8_t* lab, long long m, unsigned long long* status,
-                              int* seeds, int* entry, Counters* C, int grid, cudaStream_t s);
+                              int* seeds, int* entry, Counters* C, int grid, cudaStream_t s,
+                              bool pdl);
 long long seed_tiles(long long m);
 // Exclusive scan of per-tile pairs.  Tile count = ceil(n / tile) with n = *n_dev if
 // n_dev, else n_host.  Totals go to *tot0, *tot1.  end_mode 1: end[n] = total0;
@@ -223,9 +257,11 @@ struct PolyArrays {
   int* ntip;      // barrier-edge tips
   int* tip_h;     // barrier half-edge ending at the smallest tip vertex, or -1
   int* pcnt;      // output pieces: 0 = the polygon itself, at pos; else records at pbase
-  int* pbase;     // first piece record
+  int* pbase;     // first piece record (of a one-tip polygon, until its split: the
+                  // tip's index in the vertex sequence at pos)
   int* flen;      // total output length
-  long long* pos; // pool position of an unsplit polygon
+  long long* pos; // pool position of an unsplit polygon (or of a one-tip polygon's
+                  // sequence, before its split)
 };
 
 // Output pieces of split polygons: pool position and length (capacity n + m).
@@ -253,7 +289,7 @@ struct LongList {
 
 // lab: the label bytes (their frontier bits select the half-edges to turn)
 cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
-                        Counters* C, int grid, cudaStream_t s);
+                        Counters* C, int grid, cudaStream_t s, bool pdl);
 // One thread per seed: walk (<= kWalkCap) and, if `repair`, list polygons with
 // tips.  cap: polygons longer than cap (16, 32, 48 or 64) go to the long-polygon
 // blocks; with tips_to_long > 0 (small meshes), so do polygons with that many tips
@@ -263,7 +299,7 @@ constexpr long long kSmallMeshTri = 1ll << 16;  // meshes below this: tips_to_lo
 cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
                         const PolyArrays& P, const Pool& pool, const LongList& Lg,
                         const LongList& D1, const LongList& Dm, int cap, int repair,
-                        int tips_to_long, Counters* C, int grid, cudaStream_t s);
+                        int tips_to_long, Counters* C, int grid, cudaStream_t s, bool pdl);
 // One thread per polygon with one tip / with several tips (listed by k_walk).
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,

@@ -14,8 +14,8 @@
 //           with tips is listed -- one tip (about 90% of them) or several -- so
 //           that the dependent loads of a split do not stall the 31 other lanes of
 //           its warp; a longer one is left to one thread block (long.cu).
-//   k_repair_one    one thread per polygon with one tip: split it and chase the
-//           two arcs of the cycle at once.
+//   k_repair_one    one thread per polygon with one tip: split it and cut the
+//           two pieces out of the vertex sequence the walk left in the pool.
 //   k_repair_multi  one thread per polygon with several tips: the cycle becomes
 //           a linked list of nodes in shared memory, and each split (smallest tip
 //           of the current piece first) adds two chord nodes and relinks four
@@ -26,58 +26,66 @@
 
 namespace polylla {
 
-// Each warp takes 256 consecutive triangles at a time: their frontier half-edges
-// (label bits 2-4, 8 triangles per lane) are compacted into the warp's list in
-// shared memory by a warp scan, in increasing order, and then turned 32 at a
-// time, one per lane: no lane idles on a half-edge that is not frontier, and the
-// 32 turns of a round start at neighbouring half-edges.
-constexpr int kSuccChunk = 256;  // triangles per warp and round of compaction
-constexpr int kSuccPer = kSuccChunk / 32;
+// Each warp takes a chunk of 32 * PER consecutive triangles at a time (PER = 8
+// on large meshes): their frontier half-edges (label bits 2-4, PER triangles per
+// lane) are compacted into the warp's list in shared memory by a warp scan, in
+// increasing order, and then turned 32 at a time, one per lane: no lane idles on a
+// half-edge that is not frontier, and the 32 turns of a round start at
+// neighbouring half-edges.  On a mesh with fewer 256-triangle chunks than the
+// grid has warps, smaller chunks (PER = 4, 2, 1) give every warp work, so a warp
+// turns fewer rounds one after another.
+template <int PER>
+__device__ __forceinline__ unsigned long long load_lab(const uint8_t* __restrict__ lab,
+                                                       long long t0, long long m) {
+  unsigned long long v = 0;
+  if (t0 + PER <= m && (reinterpret_cast<uintptr_t>(lab + t0) & (PER - 1)) == 0) {
+    if (PER == 8) {
+      const uint2 w = __ldg(reinterpret_cast<const uint2*>(lab + t0));
+      v = (unsigned long long)w.x | ((unsigned long long)w.y << 32);
+    } else if (PER == 4) {
+      v = __ldg(reinterpret_cast<const unsigned*>(lab + t0));
+    } else if (PER == 2) {
+      v = __ldg(reinterpret_cast<const unsigned short*>(lab + t0));
+    } else {
+      v = __ldg(lab + t0);
+    }
+  } else {
+    for (int i = 0; i < PER && t0 + i < m; ++i)
+      v |= (unsigned long long)__ldg(lab + t0 + i) << (8 * i);
+  }
+  return v;
+}
 
+template <int PER>
 __global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const uint8_t* __restrict__ lab,
                                                  const int* __restrict__ tf,
                                                  int* __restrict__ succ, Counters* C) {
-  // half-edge offsets inside the chunk (< 3 * kSuccChunk): 16 bits leave the L1
-  // the turns read from
-  __shared__ unsigned short s_list[kBlock / 32][3 * kSuccChunk];
+  constexpr int kChunk = 32 * PER;
+  // half-edge offsets inside the chunk (< 3 * kChunk): 16 bits leave the L1 the
+  // turns read from
+  __shared__ unsigned short s_list[kBlock / 32][3 * kChunk];
+  pdl_wait();  // the label bytes and tf words
+  pdl_launch_dependents();
   const long long m = M.m;
   const int H = (int)(3 * m);
   const int lane = threadIdx.x & 31;
   unsigned short* list = s_list[threadIdx.x >> 5];
-  const long long nchunks = (m + kSuccChunk - 1) / kSuccChunk;
-  const bool aligned8 = (reinterpret_cast<uintptr_t>(lab) & 7u) == 0;
+  const long long nchunks = (m + kChunk - 1) / kChunk;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  // the label bytes of this lane's 8 triangles of chunk ch (loaded one chunk ahead)
-  auto load8 = [&](long long ch, unsigned& lo, unsigned& hi) {
-    lo = 0;
-    hi = 0;
-    if (ch >= nchunks) return;
-    const long long t0 = ch * kSuccChunk + (long long)lane * kSuccPer;
-    if (t0 + kSuccPer <= m && aligned8) {
-      const uint2 v = __ldg(reinterpret_cast<const uint2*>(lab + t0));
-      lo = v.x;
-      hi = v.y;
-    } else {
-      for (int i = 0; i < kSuccPer && t0 + i < m; ++i) {
-        const unsigned b = __ldg(lab + t0 + i);
-        if (i < 4) lo |= b << (8 * i);
-        else hi |= b << (8 * (i - 4));
-      }
-    }
+  // the label bytes of this lane's PER triangles of chunk ch (loaded one chunk ahead)
+  auto load = [&](long long ch) -> unsigned long long {
+    if (ch >= nchunks) return 0;
+    return load_lab<PER>(lab, ch * kChunk + (long long)lane * PER, m);
   };
   long long ch = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  unsigned nlo, nhi;
-  load8(ch, nlo, nhi);
+  unsigned long long next = load(ch);
   for (; ch < nchunks; ch += nwarps) {
-    const unsigned lo = nlo, hi = nhi;
-    load8(ch + nwarps, nlo, nhi);
+    const unsigned long long bytes = next;
+    next = load(ch + nwarps);
     // bit 3i + k: half-edge k of the lane's triangle i is frontier
     unsigned mask = 0;
 #pragma unroll
-    for (int i = 0; i < kSuccPer; ++i) {
-      const unsigned b = (i < 4 ? lo >> (8 * i) : hi >> (8 * (i - 4))) & 0xffu;
-      mask |= ((b >> 2) & 7u) << (3 * i);
-    }
+    for (int i = 0; i < PER; ++i) mask |= (unsigned)((bytes >> (8 * i + 2)) & 7u) << (3 * i);
     const int c = __popc(mask);
     int incl = c;
 #pragma unroll
@@ -87,14 +95,14 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const uint8_t* __res
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     int pos = incl - c;
-    const int o0 = 3 * kSuccPer * lane;  // this lane's first half-edge in the chunk
+    const int o0 = 3 * PER * lane;  // this lane's first half-edge in the chunk
     while (mask) {
       const int s = __ffs(mask) - 1;
       mask &= mask - 1;
       list[pos++] = (unsigned short)(o0 + s);
     }
     __syncwarp();
-    const int hc = (int)(3 * ch * kSuccChunk);  // the chunk's first half-edge
+    const int hc = (int)(3 * ch * kChunk);  // the chunk's first half-edge
     for (int j = lane; j < total; j += 32) {
       const int h = hc + list[j];
       const int x = __ldg(tf + h);
@@ -115,12 +123,22 @@ __global__ void __launch_bounds__(kBlock) k_succ(DevMesh M, const uint8_t* __res
   }
 }
 
-cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
-                        Counters* C, int grid, cudaStream_t s) {
+template <int PER>
+cudaError_t launch_succ_t(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
+                          Counters* C, int grid, cudaStream_t s, bool pdl) {
   static std::atomic<int> cap{0};
-  grid = resident_grid(reinterpret_cast<const void*>(k_succ), kBlock, 0, grid, &cap);
-  k_succ<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, C);
-  return cudaGetLastError();
+  grid = resident_grid(reinterpret_cast<const void*>(k_succ<PER>), kBlock, 0, grid, &cap);
+  return launch_chain(k_succ<PER>, grid, kBlock, 0, s, pdl, M, lab, tf, succ, C);
+}
+
+cudaError_t launch_succ(const DevMesh& M, const uint8_t* lab, const int* tf, int* succ,
+                        Counters* C, int grid, cudaStream_t s, bool pdl) {
+  // the largest chunk that still gives every warp of the grid at least one
+  const long long warps = (long long)grid * (kBlock / 32);
+  if (M.m >= 256 * warps) return launch_succ_t<8>(M, lab, tf, succ, C, grid, s, pdl);
+  if (M.m >= 128 * warps) return launch_succ_t<4>(M, lab, tf, succ, C, grid, s, pdl);
+  if (M.m >= 64 * warps) return launch_succ_t<2>(M, lab, tf, succ, C, grid, s, pdl);
+  return launch_succ_t<1>(M, lab, tf, succ, C, grid, s, pdl);
 }
 
 // Warp-aggregated allocation: each lane asks for `need` entries; one atomic per
@@ -165,6 +183,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
   // staging transposed (word q of thread x at q * blockDim + x): the lanes of a
   // warp, writing the same position in lockstep, hit 32 different banks
   extern __shared__ int sbuf[];
+  pdl_wait();  // the successors, seeds and entries
   int* my = sbuf + threadIdx.x;
   const long long n = C->n_seeds;
   const int H = (int)(3 * M.m);
@@ -186,7 +205,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
         prefetch_l2(succ + 3 * t0, 12 * (t1 - t0 + 1));
       }
     }
-    int len = 0, ntips = 0, tip_h = -1, rank0 = 0, start = 0;
+    int len = 0, ntips = 0, tip_h = -1, tip_s = 0, rank0 = 0, start = 0;
     bool closed = false, is_long = false;
     if (i < n) {
       int e = entry[i];
@@ -214,6 +233,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
             if (b < tipv) {
               tipv = b;
               tip_h = h;
+              tip_s = len;
             }
           }
           ++len;
@@ -235,7 +255,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
       }
     }
     const bool split = closed && repair && ntips > 0;
-    const int need = (closed && !split) ? len : 0;
+    // a one-tip polygon's vertex sequence goes to the pool too: its split cuts
+    // the two pieces out of it
+    const bool seq = split && ntips == 1;
+    const int need = (closed && (!split || seq)) ? len : 0;
     const long long off = warp_alloc(&C->pool_alloc, need);
     if (i >= n) continue;
     if (is_long) {
@@ -252,23 +275,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
     st_len += len;
     st_tips += ntips;
     st_tippolys += ntips > 0;
-    if (split) {
-      P.start[i] = start;
-      P.len[i] = len;
-      P.ntip[i] = ntips;
-      P.tip_h[i] = tip_h;
-      LongList& D = (ntips == 1) ? D1 : Dm;
-      long long* cnt = (ntips == 1) ? &C->n_defer : &C->n_multi;
-      const long long d = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cnt), 1ull);
-      if (d < D.cap) D.poly[d] = (int)i;
-      else set_error(C, POLYLLA_ERR_LIMIT, 55);
-      continue;
-    }
-    if (off + need > pool.cap) {
-      set_error(C, POLYLLA_ERR_LIMIT, 53);
-      continue;
-    }
-    {
+    if (need) {  // the sequence, rotated to the canonical start
+      if (off + need > pool.cap) {
+        set_error(C, POLYLLA_ERR_LIMIT, 53);
+        continue;
+      }
       int* out = pool.v + off;
       int r = rank0;
       for (int q = 0; q < len; ++q) {
@@ -276,8 +287,21 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
         if (++r == len) r = 0;
       }
       P.pos[i] = off;
-      P.flen[i] = len;
     }
+    if (split) {
+      P.start[i] = start;
+      P.len[i] = len;
+      P.ntip[i] = ntips;
+      P.tip_h[i] = tip_h;
+      if (seq) P.pbase[i] = tip_s >= rank0 ? tip_s - rank0 : tip_s - rank0 + len;
+      LongList& D = (ntips == 1) ? D1 : Dm;
+      long long* cnt = (ntips == 1) ? &C->n_defer : &C->n_multi;
+      const long long d = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cnt), 1ull);
+      if (d < D.cap) D.poly[d] = (int)i;
+      else set_error(C, POLYLLA_ERR_LIMIT, 55);
+      continue;
+    }
+    P.flen[i] = len;
   }
   st_len = __reduce_add_sync(0xffffffffu, st_len);
   st_tips = __reduce_add_sync(0xffffffffu, st_tips);
@@ -293,7 +317,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
 cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* succ,
                         const PolyArrays& P, const Pool& pool, const LongList& Lg,
                         const LongList& D1, const LongList& Dm, int cap, int repair,
-                        int tips_to_long, Counters* C, int grid, cudaStream_t s) {
+                        int tips_to_long, Counters* C, int grid, cudaStream_t s, bool pdl) {
   if (cap < 16 || cap > kWalkCap || cap % 16) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int) * (size_t)kWalkThreads * cap;
   static std::atomic<bool> attr{false};
@@ -305,9 +329,8 @@ cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* 
   static std::atomic<int> resident[kWalkCap / 16 + 1] = {};
   grid = resident_grid(reinterpret_cast<const void*>(k_walk), kWalkThreads, smem, grid,
                        &resident[cap / 16]);
-  k_walk<<<grid, kWalkThreads, smem, s>>>(M, tf, entry, succ, P, pool, Lg, D1, Dm, cap, repair,
-                                          tips_to_long, C);
-  return cudaGetLastError();
+  return launch_chain(k_walk, grid, kWalkThreads, smem, s, pdl, M, tf, entry, succ, P, pool, Lg, D1,
+                      Dm, cap, repair, tips_to_long, C);
 }
 
 __device__ __forceinline__ unsigned long long vkey(int origin, int h) {
@@ -318,10 +341,16 @@ __device__ __forceinline__ unsigned long long vkey(int origin, int h) {
 // pn = twin(p) = b->a.  The two pieces are
 //     oj, q, succ(q), ..., p          and          tw, pn, succ(pn), ..., pred(q)
 // (the boundary walk with oj, tw frontier); the other frontier half-edges keep
-// their turns, so both arcs follow the precomputed succ.  The arcs are chased
-// together; their origins are staged in the polygon's pool space (arc 1 from
-// the front, arc 2 from the back) and each piece is then copied from its
-// canonical start.  Pool space: 2L + 2 (pieces, then staging).
+// their turns.  The walk left the polygon's vertex sequence v (from its canonical
+// start) in the pool and the tip's index t in it (v[t] = a, v[t+1] = b).  When x
+// occurs once in v, at u, q is the half-edge leaving x there, and the pieces are
+//     b, v[u], ..., v[t]          and          x, v[t+1], ..., v[u-1]
+// (indices cyclic); each is written from its smallest vertex when that vertex
+// occurs once in it (then it is the canonical start).  Otherwise (x, or a piece's
+// smallest vertex, repeated: the canonical start needs half-edge ids) the two arcs
+// of the cycle are chased along succ at once, staged over v (arc 1 from the
+// front, arc 2 from the back), and each piece is copied from its canonical start.
+// Pool space: L + 2 for the pieces.
 __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, int* tf,
                                                        const int* __restrict__ succ, PolyArrays P,
                                                        FinalPieces F, Pool pool, LongList D1,
@@ -329,24 +358,28 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
   const long long nd = min(C->n_defer, D1.cap);
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
-  unsigned st_bad = 0;
+  unsigned st_bad = 0, st_chase = 0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < nd;
        base += (long long)gridDim.x * blockDim.x) {
     const long long d = base + threadIdx.x;
     const long long i = (d < nd) ? D1.poly[d] : -1;
     const int L = (i >= 0) ? P.len[i] : 0;
-    const long long off = warp_alloc(&C->pool_alloc, i >= 0 ? 2 * L + 2 : 0);
+    const long long off = warp_alloc(&C->pool_alloc, i >= 0 ? L + 2 : 0);
     const long long foff = warp_alloc(&C->fslot_alloc, i >= 0 ? 2 : 0);
     if (i < 0) continue;
-    if (off + 2 * L + 2 > pool.cap || foff + 2 > F.cap || L < 3) {
+    if (off + L + 2 > pool.cap || foff + 2 > F.cap || L < 3) {
       set_error(C, POLYLLA_ERR_LIMIT, 56);
       continue;
     }
     const int tp = P.tip_h[i];
-    if ((unsigned)tp >= (unsigned)H) {
+    const int t = P.pbase[i];
+    const long long vpos = P.pos[i];
+    if ((unsigned)tp >= (unsigned)H || (unsigned)t >= (unsigned)L || vpos < 0 ||
+        vpos + L > pool.cap) {
       set_error(C, POLYLLA_ERR_LIMIT, 57);
       continue;
     }
+    int* v = pool.v + vpos;
     const int pn = tf_twin(tf[tp]);
     const int b = M.tri[he_next(tp)];
     const int oj = split_edge(tf, tp, H);
@@ -362,62 +395,116 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
     }
     set_frontier(lab, tf, oj);
     set_frontier(lab, tf, tw);
-    long long steps = 0;
-    const int g = turn_tf(tf, oj, H, steps, limit);
-    if (g < 0 || g == tw || g == pn) {
-      set_error(C, POLYLLA_ERR_LIMIT, 54);
-      continue;
-    }
-    int* stage = pool.v + off + L + 2;
-    int c1 = g, c2 = pn, n1 = 0, n2 = 0;
-    bool a1 = true, a2 = true;
-    unsigned long long b1 = vkey(b, oj), b2 = vkey(x, tw);
-    int r1 = 0, r2 = 0;
-    for (int it = 0; (a1 || a2) && it < L; ++it) {
-      const int o1 = a1 ? M.tri[c1] : 0;
-      const int s1 = a1 ? succ[c1] : 0;
-      const int o2 = a2 ? M.tri[c2] : 0;
-      const int s2 = a2 ? succ[c2] : 0;
-      if (a1) {
-        stage[n1] = o1;
-        const unsigned long long k = vkey(o1, c1);
-        ++n1;
-        if (k < b1) {
-          b1 = k;
-          r1 = n1;
-        }
-        if (c1 == tp) a1 = false;
-        else c1 = s1 & kSuccMask;
-      }
-      if (a2) {
-        ++n2;
-        stage[L - n2] = o2;
-        const unsigned long long k = vkey(o2, c2);
-        if (k < b2) {
-          b2 = k;
-          r2 = n2;
-        }
-        c2 = s2 & kSuccMask;
-        if (c2 == g) a2 = false;
-      }
-      if ((unsigned)c1 >= (unsigned)H || (unsigned)c2 >= (unsigned)H) break;
-    }
-    if (a1 || a2 || n1 + n2 != L) {
-      ++st_bad;
-      continue;
-    }
-    // piece 1 = [b, stage[0..n1)], piece 2 = [x, stage[L-1], ..., stage[L-n2]]
     int* out = pool.v + off;
-    const int l1 = n1 + 1, l2 = n2 + 1;
-    int k = r1;
-    for (int q = 0; q < l1; ++q) {
-      out[q] = k ? stage[k - 1] : b;
-      if (++k == l1) k = 0;
+    int u = -1, nx = 0;
+    for (int q = 0; q < L; ++q) {
+      if (v[q] == x) {
+        u = q;
+        ++nx;
+      }
     }
-    k = r2;
-    for (int q = 0; q < l2; ++q) {
-      out[l1 + q] = k ? stage[L - k] : x;
-      if (++k == l2) k = 0;
+    bool fast = nx == 1;
+    int l1 = 0, l2 = 0, r1 = 0, r2 = 0;
+    if (fast) {
+      const int n1 = (t >= u ? t - u : t - u + L) + 1;  // v[u..t]
+      l1 = n1 + 1;
+      l2 = L - n1 + 1;
+      int m1 = b, c1 = 1, m2 = x, c2 = 1;
+      for (int j = 0, q = u; j < L; ++j) {
+        const int o = v[q];
+        if (++q == L) q = 0;
+        if (j < n1) {
+          if (o < m1) {
+            m1 = o;
+            c1 = 1;
+            r1 = 1 + j;
+          } else if (o == m1) {
+            ++c1;
+          }
+        } else if (o < m2) {
+          m2 = o;
+          c2 = 1;
+          r2 = 1 + j - n1;
+        } else if (o == m2) {
+          ++c2;
+        }
+      }
+      fast = c1 == 1 && c2 == 1;
+      if (fast) {
+        int k = r1;
+        for (int q = 0; q < l1; ++q) {  // index k >= 1: v[u + k - 1]
+          int z = u + k - 1;
+          if (z >= L) z -= L;
+          out[q] = k ? v[z] : b;
+          if (++k == l1) k = 0;
+        }
+        k = r2;
+        for (int q = 0; q < l2; ++q) {  // index k >= 1: v[t + k]
+          int z = t + k;
+          if (z >= L) z -= L;
+          out[l1 + q] = k ? v[z] : x;
+          if (++k == l2) k = 0;
+        }
+      }
+    }
+    if (!fast) {
+      ++st_chase;
+      long long steps = 0;
+      const int g = turn_tf(tf, oj, H, steps, limit);
+      if (g < 0 || g == tw || g == pn) {
+        set_error(C, POLYLLA_ERR_LIMIT, 54);
+        continue;
+      }
+      int* stage = v;  // the sequence is not read again
+      int c1 = g, c2 = pn, n1 = 0, n2 = 0;
+      bool a1 = true, a2 = true;
+      unsigned long long b1 = vkey(b, oj), b2 = vkey(x, tw);
+      for (int it = 0; (a1 || a2) && it < L; ++it) {
+        const int o1 = a1 ? M.tri[c1] : 0;
+        const int s1 = a1 ? succ[c1] : 0;
+        const int o2 = a2 ? M.tri[c2] : 0;
+        const int s2 = a2 ? succ[c2] : 0;
+        if (a1) {
+          stage[n1] = o1;
+          const unsigned long long k = vkey(o1, c1);
+          ++n1;
+          if (k < b1) {
+            b1 = k;
+            r1 = n1;
+          }
+          if (c1 == tp) a1 = false;
+          else c1 = s1 & kSuccMask;
+        }
+        if (a2) {
+          ++n2;
+          stage[L - n2] = o2;
+          const unsigned long long k = vkey(o2, c2);
+          if (k < b2) {
+            b2 = k;
+            r2 = n2;
+          }
+          c2 = s2 & kSuccMask;
+          if (c2 == g) a2 = false;
+        }
+        if ((unsigned)c1 >= (unsigned)H || (unsigned)c2 >= (unsigned)H) break;
+      }
+      if (a1 || a2 || n1 + n2 != L) {
+        ++st_bad;
+        continue;
+      }
+      // piece 1 = [b, stage[0..n1)], piece 2 = [x, stage[L-1], ..., stage[L-n2]]
+      l1 = n1 + 1;
+      l2 = n2 + 1;
+      int k = r1;
+      for (int q = 0; q < l1; ++q) {
+        out[q] = k ? stage[k - 1] : b;
+        if (++k == l1) k = 0;
+      }
+      k = r2;
+      for (int q = 0; q < l2; ++q) {
+        out[l1 + q] = k ? stage[L - k] : x;
+        if (++k == l2) k = 0;
+      }
     }
     F.pos[foff] = off;
     F.len[foff] = l1;
@@ -428,6 +515,9 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
     P.flen[i] = L + 2;
   }
   if (st_bad) set_error(C, POLYLLA_ERR_LIMIT, 58);
+  st_chase = __reduce_add_sync(0xffffffffu, st_chase);
+  if ((threadIdx.x & 31) == 0 && st_chase)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_one_chase), (unsigned long long)st_chase);
   // one split per polygon of this list
   if (blockIdx.x == 0 && threadIdx.x == 0 && nd > 0)
     atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)nd);

@@ -189,9 +189,10 @@ def tips(poly):
     return [poly[(i + 1) % n] for i in range(n) if poly[i] == poly[(i + 2) % n]]
 
 
-def check_final_mesh(mesh, polys, frontier_final, convex=True):
+def check_final_mesh(mesh, polys, frontier_final, convex=True, pinch=False):
     """Invariants of the final polygonal mesh (Section 3.2.3's output): every
-    polygon simple, ccw, with positive area; areas add up to the domain's area (the
+    polygon simple (with pinch=True: free of barrier-edge tips, since a region that
+    touches itself at a vertex keeps that vertex twice), ccw, with positive area; areas add up to the domain's area (the
     triangles' total, which is the hull's for a convex domain); the polygons' edges
     are exactly the frontier edges (each frontier half-edge in exactly one
     polygon); every vertex is used; the Euler characteristic V - E + F is the
@@ -204,7 +205,10 @@ def check_final_mesh(mesh, polys, frontier_final, convex=True):
     directed = []
     for p in polys:
         assert len(p) >= 3
-        assert len(set(p)) == len(p), f"polygon not simple: {p}"
+        if pinch:
+            assert all(p[i - 1] != p[(i + 1) % len(p)] for i in range(len(p))), f"tip left: {p}"
+        else:
+            assert len(set(p)) == len(p), f"polygon not simple: {p}"
         a = twice_area(p, xy)
         assert a > 0, f"polygon not ccw / zero area: {p}"
         tot += a
@@ -436,3 +440,13 @@ def neighbors_from_twin(mesh, convention: int = 0) -> np.ndarray:
     if convention == 0:
         cross = cross[:, [1, 2, 0]]
     return np.ascontiguousarray(cross.astype(np.int32))
+
+
+def repeated_vertex_split():
+    """tests/golden/meshes/repeated_vertex_split.json: 43 triangles cut out of a
+    Gaussian-mixture lattice mesh (its generator sits beside it), with a one-tip
+    polygon whose split edge ends at a vertex the polygon's boundary visits twice."""
+    with open(os.path.join(GOLDEN, "meshes", "repeated_vertex_split.json")) as f:
+        case = json.load(f)
+    tri = np.asarray(case["tri"], dtype=np.int32)
+    return _mesh_from(np.asarray(case["xy"], dtype=np.int64), tri)

@@ -17,7 +17,7 @@ import pytest
 
 import meshgen
 import oracle
-from meshlib import disjoint_union, spiral_wheel, tip_hub
+from meshlib import disjoint_union, repeated_vertex_split, spiral_wheel, tip_hub
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,6 +51,19 @@ def test_polygon_with_more_tips_than_the_node_list_is_split_by_rewalking():
     assert st["n_multi_seq"] == 3
     assert st["n_multi_tip"] >= 3
     assert st["n_splits"] >= 30
+
+
+def test_one_tip_split_ending_at_a_repeated_vertex_chases_the_arcs():
+    """The one-tip kernel cuts its two pieces out of the traversal's vertex
+    sequence; when the split edge ends at a vertex the polygon visits twice, the
+    sequence does not say where the second piece starts, and the kernel chases the
+    successors instead (n_one_chase).  Alone and next to an ordinary mesh."""
+    for mesh in (repeated_vertex_split(),
+                 disjoint_union([meshgen.generate("gmm", 3000, 1 << 22, 36), repeated_vertex_split()])):
+        g = assert_parity(mesh)
+        st = g["stats"]
+        assert st["n_one_chase"] == 1
+        assert st["n_one_tip"] > st["n_one_chase"] or st["n_one_tip"] == 1
 
 
 def test_small_mesh_gives_several_tip_polygons_to_the_block_kernel():

@@ -13,6 +13,7 @@ import pytest
 import meshgen
 import oracle
 from meshlib import (brute_final_polygons, brute_labels, brute_regions, check_final_mesh,
+                     repeated_vertex_split,
                      csr_to_lists, golden_cases, grid_mesh, lepp_end, spiral_wheel, tip_hub,
                      tip_order_meshes, tips)
 
@@ -64,7 +65,7 @@ def pin_grid(k, seed, lib=None):
     assert int(fr.sum()) == 3 * m - 2 * k * k
 
 
-def pin_bruteforce(mesh, lib=None, convex=True):
+def pin_bruteforce(mesh, lib=None, convex=True, pinch=False):
     r = oracle.full(mesh, lib)
     b = brute_labels(mesh)
     lab = r["label"]
@@ -87,7 +88,7 @@ def pin_bruteforce(mesh, lib=None, convex=True):
         assert edges == bnd[comp[s]], "polygon is not the region boundary"
         assert p[0] == min(p), "polygon does not start at its smallest vertex"
     final = csr_to_lists(r["off"], r["vtx"])
-    check_final_mesh(mesh, final, r["frontier_final"], convex=convex)
+    check_final_mesh(mesh, final, r["frontier_final"], convex=convex, pinch=pinch)
     assert len(final) == len(polys) + r["splits"]
     assert len(r["vtx"]) == len(r["trav_vtx"]) + 2 * r["splits"]
     return r
@@ -183,6 +184,35 @@ def test_tip_hub_has_ten_tips_on_a_short_boundary():
     assert r["splits"] == 10
     polys, fr = brute_final_polygons(mesh)
     check_final_mesh(mesh, polys, fr, convex=False)
+
+
+def test_split_edge_ending_at_a_repeated_vertex():
+    """A one-tip polygon whose split edge b -> x ends at a vertex its boundary visits
+    twice (a pinch of the region): labels, regions and the final polygons pinned by
+    brute force; x is the vertex after b in the first piece and occurs twice in the
+    traversal polygon."""
+    mesh = repeated_vertex_split()
+    pin_bruteforce(mesh, convex=False, pinch=True)
+    pin_repair_bruteforce(mesh)
+    r = oracle.full(mesh)
+    trav = csr_to_lists(r["trav_off"], r["trav_vtx"])
+    final = csr_to_lists(r["off"], r["vtx"])
+    found = False
+    j = 0
+    for v in trav:
+        t = tips(v)
+        n_pieces = 1 + (len(t) > 0)
+        if len(t) == 1:
+            b = t[0]  # the tip vertex
+            p1, p2 = final[j], final[j + 1]
+            assert len(p1) + len(p2) == len(v) + 2
+            i = next(i for i in range(len(p1)) if p1[i] == b and p1[(i + 1) % len(p1)] in p2)
+            x = p1[(i + 1) % len(p1)]
+            found |= v.count(x) == 2
+        elif len(t) > 1:
+            break  # piece counts of several-tip polygons are not needed here
+        j += n_pieces
+    assert found
 
 
 def test_trivertex_bruteforce():
