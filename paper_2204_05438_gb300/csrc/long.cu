@@ -34,19 +34,13 @@
 
 namespace polylla {
 
-// Three sizes of the block: a large one (4096 members, 4096 triangles, 512 threads,
-// about 180 KB of shared memory: one block per SM) for any region; a medium one
-// (2048 members and triangles, 256 threads, about 90 KB) that leaves room on its SM
-// for the split kernels running beside it; and a small one (512 members, 512
-// triangles, 128 threads, about 22 KB: several blocks per SM).  The medium and
-// small blocks hand a region they cannot hold to the large one.
+// Two sizes of the block: a large one (4096 members, 4096 triangles, 512 threads,
+// about 180 KB of shared memory: one block per SM) for any region, and a small
+// one (512 members, 512 triangles, 128 threads, about 22 KB: several blocks per
+// SM) that hands a region it cannot hold to the large one.
 constexpr int kLongThreads = 512;
 constexpr int kLM = 4096;  // members of one long polygon (with its split half-edges)
 constexpr int kLT = 4096;  // BFS queue: triangles of one long region
-constexpr int kMedThreads = 256;
-constexpr int kMedLM = 2048;
-constexpr int kMedLT = 2048;
-constexpr int kLargeAfterMed = 16;  // large blocks behind the medium ones (rare regions)
 constexpr int kSmallThreads = 128;
 constexpr int kSmallLM = 512;
 constexpr int kSmallLT = 512;
@@ -742,15 +736,6 @@ cudaError_t launch_long(const DevMesh& M, uint8_t* lab, int* tf, const int* seed
     return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg,
                                                  &C->n_long, none, nullptr, loc, vstamp, epoch,
                                                  repair, C, sms, s);
-  if (mode == 3) {  // medium blocks, then a few large ones for what they hand over
-    cudaError_t e = launch_long_t<kMedThreads, kMedLM, kMedLT>(
-        M, lab, tf, seeds, succ, P, F, pool, Lg, &C->n_long, Lg2, &C->n_long2, loc, vstamp, epoch,
-        repair, C, sms, s);
-    if (e != cudaSuccess) return e;
-    return launch_long_t<kLongThreads, kLM, kLT>(M, lab, tf, seeds, succ, P, F, pool, Lg2,
-                                                 &C->n_long2, none, nullptr, loc, vstamp, epoch,
-                                                 repair, C, kLargeAfterMed, s);
-  }
   // small blocks (mode 1) or one warp per polygon (mode 2) first; the regions
   // they cannot hold, in large blocks
   cudaError_t e =

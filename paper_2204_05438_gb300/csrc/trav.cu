@@ -160,6 +160,21 @@ __device__ __forceinline__ long long warp_alloc(long long* counter, int need) {
 }
 
 
+// Warp-aggregated list append: each lane with `want` gets its own slot of the
+// list counted by `counter` (one atomic per warp, slots in lane order), the
+// others -1.  All 32 lanes must call it.
+__device__ __forceinline__ long long warp_append(long long* counter, bool want) {
+  const unsigned b = __ballot_sync(0xffffffffu, want);
+  if (b == 0) return -1;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(b) - 1;
+  unsigned long long base = 0;
+  if (lane == leader)
+    base = atomicAdd(reinterpret_cast<unsigned long long*>(counter), (unsigned long long)__popc(b));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return want ? (long long)base + __popc(b & ((1u << lane) - 1u)) : -1;
+}
+
 // Triangle of a seed's entry word (3t + k, or -1 - t)
 __device__ __forceinline__ long long entry_tri(int e) { return e >= 0 ? e / 3 : -1 - (long long)e; }
 
@@ -260,12 +275,15 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
     const bool seq = split && ntips == 1;
     const int need = (closed && (!split || seq)) ? len : 0;
     const long long off = warp_alloc(&C->pool_alloc, need);
+    // list slots, one atomic per warp and list
+    const long long jl = warp_append(&C->n_long, i < n && is_long);
+    const long long j1 = warp_append(&C->n_defer, i < n && split && ntips == 1);
+    const long long jm = warp_append(&C->n_multi, i < n && split && ntips > 1);
     if (i >= n) continue;
     if (is_long) {
       P.pcnt[i] = 0;
       P.flen[i] = 0;
-      const long long j = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_long), 1ull);
-      if (j < Lg.cap) Lg.poly[j] = (int)i;
+      if (jl < Lg.cap) Lg.poly[jl] = (int)i;
       continue;
     }
     // start, length and tips are read only by the reparation kernels
@@ -278,6 +296,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
     if (need) {  // the sequence, rotated to the canonical start
       if (off + need > pool.cap) {
         set_error(C, POLYLLA_ERR_LIMIT, 53);
+        if (seq && j1 < D1.cap) {  // its list slot is taken: a record the split skips
+          P.len[i] = 0;
+          D1.poly[j1] = (int)i;
+        }
         continue;
       }
       int* out = pool.v + off;
@@ -295,8 +317,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
       P.tip_h[i] = tip_h;
       if (seq) P.pbase[i] = tip_s >= rank0 ? tip_s - rank0 : tip_s - rank0 + len;
       LongList& D = (ntips == 1) ? D1 : Dm;
-      long long* cnt = (ntips == 1) ? &C->n_defer : &C->n_multi;
-      const long long d = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(cnt), 1ull);
+      const long long d = (ntips == 1) ? j1 : jm;
       if (d < D.cap) D.poly[d] = (int)i;
       else set_error(C, POLYLLA_ERR_LIMIT, 55);
       continue;
