@@ -608,73 +608,90 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
       __syncthreads();
       continue;
     }
+    // one thread merges, in decreasing tip order, the two trees the chord joins:
+    // top[] is the tree of a representative leaf, cnt[] a tree's leaf count,
+    // up[] a node's parent and inc[] what a leaf below its right child adds to its
+    // position; the leaves then climb to the root in parallel
+    int* top = pos;
+    int* up = left;
+    int* inc = right;
+    int* ch = uf + npieces;  // the leaves on either side of chord q: ch[2q], ch[2q + 1]
     for (int v = threadIdx.x; v < npieces; v += blockDim.x) {
       uf[v] = v;
-      pos[v] = v;
+      top[v] = v;
+      cnt[v] = 1;
     }
-    for (int q = threadIdx.x; q < ns; q += blockDim.x) {  // the leaves on either side of chord q
-      cnt[2 * q] = nodeof[B[A[L + 2 * q]] - L];
-      cnt[2 * q + 1] = nodeof[B[A[L + 2 * q + 1]] - L];
+    for (int q = threadIdx.x; q < ns; q += blockDim.x) {
+      ch[2 * q] = nodeof[B[A[L + 2 * q]] - L];
+      ch[2 * q + 1] = nodeof[B[A[L + 2 * q + 1]] - L];
     }
     __syncthreads();
+    if (threadIdx.x == (blockDim.x > 32 ? 32 : 0)) {  // beside the merging thread
+      s_base = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->pool_alloc),
+                                    (unsigned long long)N);
+      s_fbase = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&C->fslot_alloc),
+                                     (unsigned long long)npieces);
+    }
+    const int W = 2 * ns + 1;
     if (threadIdx.x == 0) {
-      const long long base = (long long)atomicAdd(
-          reinterpret_cast<unsigned long long*>(&C->pool_alloc), (unsigned long long)N);
-      const long long fb = (long long)atomicAdd(
-          reinterpret_cast<unsigned long long*>(&C->fslot_alloc), (unsigned long long)npieces);
-      const int W = 2 * ns + 1;
       int nodes = npieces;
-      bool bad = false;
       for (int q = ns - 1; q >= 0; --q) {  // decreasing tip vertex
-        int ra = cnt[2 * q];
-        int rb = cnt[2 * q + 1];
+        int ra = ch[2 * q];
+        int rb = ch[2 * q + 1];
         while (uf[ra] != ra) ra = uf[ra] = uf[uf[ra]];
         while (uf[rb] != rb) rb = uf[rb] = uf[uf[rb]];
         if (ra == rb || nodes >= W) {
-          bad = true;
+          set_error(C, POLYLLA_ERR_LIMIT, 111);
+          s_fail = 1;
           break;
         }
         const int u = nodes++;
-        left[u] = pos[ra];
-        right[u] = pos[rb];
+        const int ta = top[ra], tb = top[rb];
+        const int ca = cnt[ta];
+        up[ta] = u;
+        inc[ta] = 0;
+        up[tb] = u;
+        inc[tb] = ca;
+        cnt[u] = ca + cnt[tb];
         uf[rb] = ra;
-        pos[ra] = u;
+        top[ra] = u;
       }
-      if (bad) {
-        set_error(C, POLYLLA_ERR_LIMIT, 111);
-        s_fail = 1;
-      } else {
-        for (int v = 0; v < npieces; ++v) cnt[v] = 1;  // subtree sizes (in leaves)
-        for (int u = npieces; u < nodes; ++u) cnt[u] = cnt[left[u]] + cnt[right[u]];
-        pos[nodes - 1] = 0;
-        for (int u = nodes - 1; u >= npieces; --u) {
-          pos[left[u]] = pos[u];
-          pos[right[u]] = pos[u] + cnt[left[u]];
-        }
-        if (base + N > pool.cap || fb + npieces > F.cap) {
-          set_error(C, POLYLLA_ERR_LIMIT, 112);
-          s_fail = 1;
-        } else {
-          s_base = base;
-          s_fbase = fb;
-          P.pcnt[i] = npieces;
-          P.pbase[i] = (int)fb;
-          P.flen[i] = N;
-          atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)ns);
-        }
-      }
+      if (!s_fail) up[nodes - 1] = -1;  // the root
     }
     __syncthreads();
-    if (s_fail) {
+    const long long base = s_base, fb = s_fbase;
+    if (s_fail || base + N > pool.cap || fb + npieces > F.cap) {
+      if (threadIdx.x == 0 && !s_fail) set_error(C, POLYLLA_ERR_LIMIT, 112);
       __syncthreads();
       continue;
     }
-    for (int v = threadIdx.x; v < npieces; v += blockDim.x)  // lengths in output order
-      cnt[pos[v]] = dist[A[node_name[v]]] + 1;
+    for (int v = threadIdx.x; v < npieces; v += blockDim.x) {  // position, then length there
+      int p = 0;
+      for (int x = v, k = 0; up[x] >= 0 && k < W; ++k) {
+        p += inc[x];
+        x = up[x];
+      }
+      if (p < npieces) {
+        pos[v] = p;
+        cnt[p] = dist[A[node_name[v]]] + 1;
+      } else {
+        s_fail = 1;
+      }
+    }
     __syncthreads();
+    if (s_fail) {  // not a tree: left as an error (no record was written)
+      if (threadIdx.x == 0) set_error(C, POLYLLA_ERR_LIMIT, 114);
+      __syncthreads();
+      continue;
+    }
+    if (threadIdx.x == 0) {
+      P.pcnt[i] = npieces;
+      P.pbase[i] = (int)fb;
+      P.flen[i] = N;
+      atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)ns);
+    }
     if (threadIdx.x < 32) {  // offsets and piece records
       const int lane = threadIdx.x;
-      const long long base = s_base, fb = s_fbase;
       int acc = 0;
       for (int p0 = 0; p0 < npieces; p0 += 32) {
         const int p = p0 + lane;
@@ -695,7 +712,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
     }
     __syncthreads();
     // ---- 4g. members to the pool: piece offset + rank from the piece's start
-    const long long base = s_base;
     for (int a = threadIdx.x; a < N; a += blockDim.x) {
       const int s0 = A[a];
       const int node = nodeof[B[s0] - L];
