@@ -111,6 +111,8 @@ typedef struct {
   int64_t n_one_chase;    /* one-tip polygons whose pieces could not be cut out of the
                              traversal's vertex sequence (a repeated vertex), split by
                              chasing the successors */
+  int64_t n_multi_turn;   /* pieces of several-tip polygons whose smallest vertex
+                             repeats, their half-edges found by turning */
 } polylla_stats;
 
 /*
@@ -479,6 +481,18 @@ polylla_status polylla_server_destroy(polylla_server_t server);
  * had allocated.
  */
 void polylla_debug_fail_alloc(int64_t k);
+
+/*
+ * Test switch (Section 3.2.3's split, its rarer device paths): with enable != 0,
+ * the reparation of this handle takes the paths normally kept for polygons with
+ * a repeated vertex on every polygon -- one-tip pieces by chasing the successors
+ * (counted in n_one_chase), several-tip pieces ordered by (origin, half-edge) with
+ * half-edges found by turning (n_multi_turn), and each split's far node found
+ * through turn(oj) -- so that tests can compare those paths with the oracle on any
+ * mesh.  The polygons are the same either way.  Errors: POLYLLA_ERR_INVALID_ARG
+ * for a null handle.
+ */
+polylla_status polylla_debug_rare_paths(polylla_mesh_t mesh, int enable);
 
 #ifdef __cplusplus
 }

@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n_seeds", "n_poly_trav", "n_vtx_trav", "n_tip_polygons", "n_tips", "n_splits",
         "n_poly", "n_vtx", "n_long", "n_long_handoff", "n_long_seq", "n_one_tip", "n_multi_tip",
-        "n_multi_seq", "n_one_chase")]
+        "n_multi_seq", "n_one_chase", "n_multi_turn")]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -133,6 +133,7 @@ def load_library(path: str | None = None):
             "polylla_server_info": ([vp, ctypes.POINTER(ServerStats)], st),
             "polylla_server_cancel": ([vp, i64], st),
             "polylla_debug_fail_alloc": ([i64], None),
+            "polylla_debug_rare_paths": ([vp, i32], st),
             "polylla_server_destroy": ([vp], st),
             "polylla_lepp": ([vp, vp], st),
             "polylla_mesh_build_twin": ([vp, vp], st),
@@ -547,6 +548,12 @@ def debug_fail_alloc(k: int):
     """Failure injection for tests: the k-th device allocation from now on fails
     (k <= 0: off)."""
     load_library().polylla_debug_fail_alloc(k)
+
+
+def debug_rare_paths(mesh: int, enable: bool = True):
+    """Test switch: the reparation takes its repeated-vertex paths on every
+    polygon (same polygons; see the header)."""
+    _check(load_library().polylla_debug_rare_paths(mesh, int(enable)), "polylla_debug_rare_paths")
 
 
 def server_destroy(server: int):

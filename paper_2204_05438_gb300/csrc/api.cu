@@ -86,6 +86,7 @@ struct polylla_mesh {
   // schedule: the walk's thread-per-seed cap and the long-polygon mode
   int walk_cap = kWalkCap;
   bool overlap = true;  // the kernels after the walk on side streams
+  bool rare_paths = false;  // polylla_debug_rare_paths
   int long_mode = 0;
   bool lepp_valid = false;
   long long* obase = nullptr;  // batches: output index of each traversal polygon
@@ -429,11 +430,13 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   }));
   if (repair) {
     POLY_TRY(launch(h, "repair_multi", s2, [&] {
-      return launch_repair_multi(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dm, h->C,
+      return launch_repair_multi(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dm,
+                                 h->rare_paths, h->C,
                                  h->sms, s2);
     }));
     POLY_TRY(launch(h, "repair_one", s, [&] {
-      return launch_repair_one(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dl, h->C,
+      return launch_repair_one(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dl,
+                               h->rare_paths, h->C,
                                h->sms, s);
     }));
   }
@@ -641,6 +644,12 @@ polylla_status batch_table(polylla_batch* b) {
 extern "C" {
 
 void polylla_debug_fail_alloc(int64_t k) { g_fail_alloc.store(k > 0 ? k : 0); }
+
+polylla_status polylla_debug_rare_paths(polylla_mesh_t h, int enable) {
+  if (!h) return POLYLLA_ERR_INVALID_ARG;
+  h->rare_paths = enable != 0;
+  return POLYLLA_OK;
+}
 
 const char* polylla_status_str(polylla_status st) {
   switch (st) {
@@ -937,6 +946,7 @@ polylla_status polylla_get_stats(polylla_mesh_t h, polylla_stats* out) {
     out->n_multi_tip = c.n_multi;
     out->n_multi_seq = c.n_multi_seq;
     out->n_one_chase = c.n_one_chase;
+    out->n_multi_turn = c.n_multi_turn;
   }
   return POLYLLA_OK;
 }

@@ -47,6 +47,7 @@ struct Counters {
   long long n_long_seq;   // long regions too large for a block, walked by one thread
   long long n_multi_seq;  // several-tip polygons with more tips than the node list holds
   long long n_one_chase;  // one-tip polygons split by chasing (a repeated vertex)
+  long long n_multi_turn; // several-tip pieces with a repeated smallest vertex
   long long seed_ticket;  // tile tickets of the seed compaction's look-back
   long long seed_done;    // its completed look-backs (the last one clears the status)
   long long out_done;     // the output pass's completed look-backs (likewise)
@@ -303,10 +304,12 @@ cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* 
 // One thread per polygon with one tip / with several tips (listed by k_walk).
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                              const LongList& D1, Counters* C, int sms, cudaStream_t s);
+                              const LongList& D1, int rare, Counters* C, int sms,
+                              cudaStream_t s);
 cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                                 const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                                const LongList& Dm, Counters* C, int sms, cudaStream_t s);
+                                const LongList& Dm, int rare, Counters* C, int sms,
+                                cudaStream_t s);
 // One block per long polygon: gather, rank and, if `repair`, split.  mode 0:
 // large blocks only; mode 1: small blocks first, the regions they cannot hold
 // (listed in Lg2) then in large blocks; mode 2: the same with one-warp blocks

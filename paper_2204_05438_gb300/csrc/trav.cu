@@ -160,6 +160,11 @@ __device__ __forceinline__ long long warp_alloc(long long* counter, int need) {
 }
 
 
+// Polygons with more tips than this are split by one thread re-walking its pieces
+// (repair_seq); those with 2..kRsMaxSplit tips get the walk's tip records and the
+// several-tip kernel's node list.
+constexpr int kRsMaxSplit = 8;
+
 // Warp-aggregated list append: each lane with `want` gets its own slot of the
 // list counted by `counter` (one atomic per warp, slots in lane order), the
 // others -1.  All 32 lanes must call it.
@@ -244,6 +249,12 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
           const int g = sg & kSuccMask;
           if (sg & kTipFlag) {
             ++ntips;
+            // tip record k (its half-edge and step), staged from the top while
+            // the origins below have not reached it
+            if (ntips <= kRsMaxSplit && cap - 2 * ntips > len) {
+              my[(cap - 2 * ntips) * kWalkThreads] = h;
+              my[(cap - 2 * ntips + 1) * kWalkThreads] = len;
+            }
             const int b = M.tri[g];  // dest(h) = origin(twin(h))
             if (b < tipv) {
               tipv = b;
@@ -273,7 +284,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
     // a one-tip polygon's vertex sequence goes to the pool too: its split cuts
     // the two pieces out of it
     const bool seq = split && ntips == 1;
-    const int need = (closed && (!split || seq)) ? len : 0;
+    // a polygon with 2..kRsMaxSplit tips whose records all stayed above its
+    // origins: the sequence and the records (rotated tip index, tip half-edge)
+    // go to the pool, where the several-tip kernel also writes its pieces
+    const bool rec = split && ntips >= 2 && ntips <= kRsMaxSplit && len + 2 * ntips <= cap;
+    const int need = (closed && (!split || seq)) ? len : (rec ? len + 2 * ntips : 0);
     const long long off = warp_alloc(&C->pool_alloc, need);
     // list slots, one atomic per warp and list
     const long long jl = warp_append(&C->n_long, i < n && is_long);
@@ -296,9 +311,14 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
     if (need) {  // the sequence, rotated to the canonical start
       if (off + need > pool.cap) {
         set_error(C, POLYLLA_ERR_LIMIT, 53);
-        if (seq && j1 < D1.cap) {  // its list slot is taken: a record the split skips
+        // its list slot is taken: a record the split kernels skip
+        if (seq && j1 < D1.cap) {
           P.len[i] = 0;
           D1.poly[j1] = (int)i;
+        }
+        if (rec && jm < Dm.cap) {
+          P.len[i] = 0;
+          Dm.poly[jm] = (int)i;
         }
         continue;
       }
@@ -308,6 +328,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
         out[q] = my[r * kWalkThreads];
         if (++r == len) r = 0;
       }
+      for (int k = 1; rec && k <= ntips; ++k) {
+        const int st = my[(cap - 2 * k + 1) * kWalkThreads];
+        out[len + 2 * (k - 1)] = st >= rank0 ? st - rank0 : st - rank0 + len;
+        out[len + 2 * (k - 1) + 1] = my[(cap - 2 * k) * kWalkThreads];
+      }
       P.pos[i] = off;
     }
     if (split) {
@@ -316,6 +341,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(DevMesh M, int* tf,
       P.ntip[i] = ntips;
       P.tip_h[i] = tip_h;
       if (seq) P.pbase[i] = tip_s >= rank0 ? tip_s - rank0 : tip_s - rank0 + len;
+      else P.pbase[i] = rec ? 1 : 0;  // several tips: records at pos, or none
       LongList& D = (ntips == 1) ? D1 : Dm;
       const long long d = (ntips == 1) ? j1 : jm;
       if (d < D.cap) D.poly[d] = (int)i;
@@ -375,7 +401,7 @@ __device__ __forceinline__ unsigned long long vkey(int origin, int h) {
 __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, int* tf,
                                                        const int* __restrict__ succ, PolyArrays P,
                                                        FinalPieces F, Pool pool, LongList D1,
-                                                       Counters* C) {
+                                                       int rare, Counters* C) {
   const long long nd = min(C->n_defer, D1.cap);
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
@@ -424,7 +450,7 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
         ++nx;
       }
     }
-    bool fast = nx == 1;
+    bool fast = nx == 1 && !rare;
     int l1 = 0, l2 = 0, r1 = 0, r2 = 0;
     if (fast) {
       const int n1 = (t >= u ? t - u : t - u + L) + 1;  // v[u..t]
@@ -561,8 +587,19 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
 // A split removes the tip at p, and the one at qp if x was a tip, and creates
 // none (x always has a frontier edge of the region besides the chord), so only
 // those two flags change.
+//
+// The node list comes from the walk's records when it left them (the origins
+// from the canonical start, and each tip's index and half-edge): the other
+// nodes' half-edges stay unknown (kSuccMask) unless needed.  q is the piece's
+// only node with origin x; when x occurs more than once in the piece, q is the
+// one whose successor's origin is dest(turn(oj)) (a directed edge occurs once in
+// a boundary).  A finished piece starts at its smallest vertex; when that vertex
+// occurs more than once, the piece's half-edges are found by turning from a node
+// whose half-edge is known (a chord), and the smallest (origin, half-edge) key
+// decides.  Without records the list is built by chasing the successors.  The
+// pieces are written over the records (as long as the polygon and its tip
+// records, at least its final length).
 constexpr int kRsThreads = 64;
-constexpr int kRsMaxSplit = 8;  // more tips: the walking repair_seq
 constexpr int kRsNodes = kWalkCap + 2 * kRsMaxSplit;
 constexpr int kRsList = kRsMaxSplit + 2;
 constexpr size_t kRsSmem =
@@ -571,7 +608,7 @@ constexpr size_t kRsSmem =
 __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t* lab, int* tf,
                                                              const int* __restrict__ succ,
                                                              PolyArrays P, FinalPieces F,
-                                                             Pool pool, LongList Dm,
+                                                             Pool pool, LongList Dm, int rare,
                                                              Counters* C) {
   extern __shared__ int rs_smem[];
   int* nh = rs_smem;                                   // [kRsNodes][kRsThreads]
@@ -588,22 +625,25 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
   const long long nd = min(C->n_multi, Dm.cap);
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
-  unsigned st_splits = 0, st_seq = 0;
+  unsigned st_splits = 0, st_seq = 0, st_turn = 0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < nd;
        base += (long long)gridDim.x * blockDim.x) {
     const long long d = base + t;
     const long long i = (d < nd) ? Dm.poly[d] : -1;
     const int L = (i >= 0) ? P.len[i] : 0;
     const int nt = (i >= 0) ? P.ntip[i] : 0;
-    const long long off = warp_alloc(&C->pool_alloc, i >= 0 ? L + 2 * nt : 0);
+    const bool listed = nt <= kRsMaxSplit && L <= kWalkCap;
+    const bool rec = i >= 0 && listed && nt >= 2 && L >= 3 && P.pbase[i] == 1;
+    const long long off0 = warp_alloc(&C->pool_alloc, i >= 0 && !rec ? L + 2 * nt : 0);
     const long long foff = warp_alloc(&C->fslot_alloc, i >= 0 ? nt + 1 : 0);
     if (i < 0) continue;
-    if (off + L + 2 * nt > pool.cap || foff + nt + 1 > F.cap) {
+    const long long off = rec ? P.pos[i] : off0;
+    if (L < 3 || off < 0 || off + L + 2 * nt > pool.cap || foff + nt + 1 > F.cap) {
       set_error(C, POLYLLA_ERR_LIMIT, 56);
       continue;
     }
     int cnt;
-    if (nt > kRsMaxSplit || L > kWalkCap || L < 3) {
+    if (!listed) {
       ++st_seq;
       const Cyc first{P.start[i], L, P.tip_h[i], nt, true};
       cnt = repair_seq(M.tri, tf, lab, first, nt + 1, H, limit, F.h + foff, F.pos + foff,
@@ -611,7 +651,23 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
     } else {
       cnt = -1;
       bool bad = false;
-      {
+      if (rec) {  // the walk's records
+        const int* rv = pool.v + off;
+        for (int j = 0; j < L; ++j) {
+          NH(j) = kSuccMask;
+          NO(j) = rv[j];
+          NX(j) = (uint8_t)(j + 1 == L ? 0 : j + 1);
+          PV(j) = (uint8_t)(j == 0 ? L - 1 : j - 1);
+        }
+        for (int k = 0; k < nt; ++k) {
+          const int ix = rv[L + 2 * k], hh = rv[L + 2 * k + 1];
+          if ((unsigned)ix >= (unsigned)L || (unsigned)hh >= (unsigned)H) {
+            bad = true;
+            break;
+          }
+          NH(ix) = hh | kTipFlag;
+        }
+      } else {  // chase the successors from the canonical start
         int h = P.start[i];
         for (int j = 0; j < L; ++j) {
           if ((unsigned)h >= (unsigned)H) {
@@ -634,8 +690,8 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
       int j = 0;
       while (!bad && j < count) {
         const int s0 = PS(j);
-        int tb = 0x7fffffff, tipn = -1, keyn = s0, len = 0;
-        unsigned long long best = ~0ull;
+        // the piece: its smallest tip, its smallest vertex and how often it occurs
+        int tb = 0x7fffffff, tipn = -1, mo = 0x7fffffff, mn = s0, mc = 0, len = 0;
         int v = s0;
         do {
           const int x = NH(v);
@@ -647,10 +703,13 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
               tipn = v;
             }
           }
-          const unsigned long long key = vkey(NO(v), x & kSuccMask);
-          if (key < best) {
-            best = key;
-            keyn = v;
+          const int o = NO(v);
+          if (o < mo) {
+            mo = o;
+            mn = v;
+            mc = 1;
+          } else if (o == mo) {
+            ++mc;
           }
           ++len;
           v = nv;
@@ -660,8 +719,40 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
           break;
         }
         if (tipn < 0) {  // finished piece: its origins from the canonical start
+          if (mc > 1 || rare) {  // the smallest vertex repeats: compare (origin, half-edge)
+            ++st_turn;
+            int c0 = -1;
+            v = s0;
+            for (int k = 0; k < len && c0 < 0; ++k, v = NX(v))
+              if ((NH(v) & kSuccMask) != kSuccMask) c0 = v;
+            if (c0 < 0) {
+              bad = true;
+              break;
+            }
+            v = c0;
+            for (int k = 0; k + 1 < len && !bad; ++k) {  // unknown half-edges by turning
+              const int nv = NX(v);
+              if ((NH(nv) & kSuccMask) == kSuccMask) {
+                long long steps = 0;
+                const int g = turn_tf(tf, NH(v) & kSuccMask, H, steps, limit);
+                if (g < 0) bad = true;
+                else NH(nv) = g;
+              }
+              v = nv;
+            }
+            if (bad) break;
+            unsigned long long best = ~0ull;
+            v = s0;
+            for (int k = 0; k < len; ++k, v = NX(v)) {
+              const unsigned long long key = vkey(NO(v), NH(v) & kSuccMask);
+              if (key < best) {
+                best = key;
+                mn = v;
+              }
+            }
+          }
           int* out = pool.v + off + acc;
-          v = keyn;
+          v = mn;
           for (int k = 0; k < len; ++k) {
             out[k] = NO(v);
             v = NX(v);
@@ -688,20 +779,33 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
         }
         set_frontier(lab, tf, oj);
         set_frontier(lab, tf, tw);
-        long long steps = 0;
-        const int g = turn_tf(tf, oj, H, steps, limit);
-        if (g < 0 || g == tw) {
-          bad = true;
-          break;
+        const int x = M.tri[tw];  // origin of tw = dest(oj)
+        // q: the piece's node leaving x at turn(oj)
+        int q = -1, nq = 0;
+        v = s0;
+        for (int k = 0; k < len; ++k, v = NX(v)) {
+          if (NO(v) == x) {
+            q = v;
+            ++nq;
+          }
         }
-        int q = -1;
-        for (int k = 0; k < L; ++k)
-          if ((NH(k) & kSuccMask) == g) q = k;
-        for (int k = kWalkCap; k < nn; ++k)
-          if (NH(k) == g) q = k;
-        if (q < 0) {
-          bad = true;
-          break;
+        if (nq != 1 || rare) {  // x repeats: the node whose edge is x -> dest(turn(oj))
+          long long steps = 0;
+          const int g = turn_tf(tf, oj, H, steps, limit);
+          if (g < 0 || g == tw) {
+            bad = true;
+            break;
+          }
+          const int y = M.tri[he_next(g)];
+          q = -1;
+          v = s0;
+          for (int k = 0; k < len; ++k, v = NX(v))
+            if (NO(v) == x && NO(NX(v)) == y) q = v;
+          if (q < 0) {
+            bad = true;
+            break;
+          }
+          if ((NH(q) & kSuccMask) == kSuccMask) NH(q) = g;
         }
         const int qp = PV(q);
         const int pn = NX(tipn);
@@ -710,7 +814,7 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
         NH(u) = oj;
         NO(u) = tb;
         NH(w) = tw;
-        NO(w) = M.tri[tw];
+        NO(w) = x;
         NX(tipn) = (uint8_t)u;
         PV(u) = (uint8_t)tipn;
         NX(u) = (uint8_t)q;
@@ -748,21 +852,26 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
     atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_splits), (unsigned long long)st_splits);
   if ((threadIdx.x & 31) == 0 && st_seq)
     atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_multi_seq), (unsigned long long)st_seq);
+  st_turn = __reduce_add_sync(0xffffffffu, st_turn);
+  if ((threadIdx.x & 31) == 0 && st_turn)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&C->n_multi_turn), (unsigned long long)st_turn);
 }
 
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                              const LongList& D1, Counters* C, int sms, cudaStream_t s) {
+                              const LongList& D1, int rare, Counters* C, int sms,
+                              cudaStream_t s) {
   static std::atomic<int> cap{0};
   const int grid = resident_grid(reinterpret_cast<const void*>(k_repair_one), kBlock, 0,
                                  (long long)sms * 8, &cap);
-  k_repair_one<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, P, F, pool, D1, C);
+  k_repair_one<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, P, F, pool, D1, rare, C);
   return cudaGetLastError();
 }
 
 cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                                 const PolyArrays& P, const FinalPieces& F, const Pool& pool,
-                                const LongList& Dm, Counters* C, int sms, cudaStream_t s) {
+                                const LongList& Dm, int rare, Counters* C, int sms,
+                                cudaStream_t s) {
   static std::atomic<bool> attr{false};
   if (!attr.load()) {
     cudaFuncSetAttribute(k_repair_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -771,7 +880,7 @@ cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const i
   }
   const int per_sm = (int)((220 * 1024) / (kRsSmem + 1024));
   const int grid = sms * (per_sm < 1 ? 1 : per_sm);
-  k_repair_multi<<<grid, kRsThreads, kRsSmem, s>>>(M, lab, tf, succ, P, F, pool, Dm, C);
+  k_repair_multi<<<grid, kRsThreads, kRsSmem, s>>>(M, lab, tf, succ, P, F, pool, Dm, rare, C);
   return cudaGetLastError();
 }
 

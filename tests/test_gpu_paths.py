@@ -66,6 +66,38 @@ def test_one_tip_split_ending_at_a_repeated_vertex_chases_the_arcs():
         assert st["n_one_tip"] > st["n_one_chase"] or st["n_one_tip"] == 1
 
 
+@pytest.mark.parametrize("which", ["gmm-3k", "uniform-40k", "repeated-vertex", "hub+uniform"])
+def test_rare_split_paths_give_the_same_polygons(which):
+    """With the test switch on, every one-tip polygon is split by chasing the
+    successors, every several-tip piece is ordered by (origin, half-edge) keys with
+    its half-edges found by turning, and every split finds its far node through
+    turn(oj): the paths kept for repeated vertices, run on whole meshes against the
+    oracle (below 2^16 triangles the several-tip kernel sees two-tip polygons only,
+    above it up to eight)."""
+    mesh = {"gmm-3k": lambda: meshgen.generate("gmm", 3000, 1 << 22, 37),
+            "uniform-40k": lambda: meshgen.generate("uniform", 40_000, 1 << 22, 38),
+            "repeated-vertex": repeated_vertex_split,
+            "hub+uniform": lambda: disjoint_union([tip_hub(), meshgen.generate("uniform", 40_000, 1 << 22, 39)]),
+            }[which]()
+    ref = oracle.run(mesh)
+    M = pg.from_numpy(mesh)
+    pg.debug_rare_paths(M.handle, True)
+    for _ in range(2):
+        M.run()
+        off, vtx = (t.cpu().numpy() for t in M.polygons())
+        np.testing.assert_array_equal(off, ref["off"])
+        np.testing.assert_array_equal(vtx, ref["vtx"])
+    st = M.stats()
+    assert st["n_one_chase"] == st["n_one_tip"]
+    if st["n_multi_tip"] > st["n_multi_seq"]:
+        assert st["n_multi_turn"] >= 2 * (st["n_multi_tip"] - st["n_multi_seq"])
+    pg.debug_rare_paths(M.handle, False)
+    M.run()
+    off, vtx = (t.cpu().numpy() for t in M.polygons())
+    np.testing.assert_array_equal(vtx, ref["vtx"])
+    M.close()
+
+
 def test_small_mesh_gives_several_tip_polygons_to_the_block_kernel():
     """Below 2^16 triangles, polygons with three or more tips are split by one thread
     block each (the tips in parallel) instead of one thread; the result is the same."""
