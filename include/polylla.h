@@ -295,8 +295,7 @@ int64_t polylla_launch_count(polylla_mesh_t mesh);
  * call on that device (the CUDA runtime loads device code lazily): that first call
  * allocates their device memory and may synchronise the device.  A caller that
  * reserves all device memory for its own arena therefore makes one call (on any
- * small mesh) per device before reserving it, and before any stream capture;
- * later calls allocate nothing.  The array's address is looked up on every call
+ * small mesh) per device before reserving it; later calls allocate nothing.  The array's address is looked up on every call
  * with the calling device current.  Every call shares the one array and clears
  * what must start at zero, so calls that overlap on the GPU race and must be
  * serialised by the caller.  Each call waits for `stream` to finish before

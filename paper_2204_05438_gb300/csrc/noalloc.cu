@@ -22,8 +22,7 @@
 //     cudaGetSymbolAddress, or its first launch): that first call allocates the
 //     module's device memory and may synchronise the device.  A caller that
 //     reserves all device memory for its own arena makes one call (any small mesh)
-//     on each device before reserving it, and before any stream capture; after
-//     that no call allocates.  The module then stays loaded on that device until
+//     on each device before reserving it; after that no call allocates.  The module then stays loaded on that device until
 //     the process exits (or the caller resets the device);
 //   * every call on a device uses the same array and leaves its contents behind;
 //     the parts that must start at zero (the error word, the counters and the
