@@ -384,6 +384,8 @@ __device__ __forceinline__ unsigned long long vkey(int origin, int h) {
   return ((unsigned long long)(unsigned)origin << 32) | (unsigned)h;
 }
 
+constexpr int kSeqChunk = 4;  // sequence entries loaded at a time by the split kernels
+
 // One tip p = a->b, split along oj = b->x (tw = x->b), with q = turn(oj) and
 // pn = twin(p) = b->a.  The two pieces are
 //     oj, q, succ(q), ..., p          and          tw, pn, succ(pn), ..., pred(q)
@@ -443,11 +445,19 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
     set_frontier(lab, tf, oj);
     set_frontier(lab, tf, tw);
     int* out = pool.v + off;
+    // the passes over the sequence load kSeqChunk entries at a time, so that
+    // their latencies overlap
     int u = -1, nx = 0;
-    for (int q = 0; q < L; ++q) {
-      if (v[q] == x) {
-        u = q;
-        ++nx;
+    for (int q0 = 0; q0 < L; q0 += kSeqChunk) {
+      int w[kSeqChunk];
+#pragma unroll
+      for (int k = 0; k < kSeqChunk; ++k) w[k] = (q0 + k < L) ? v[q0 + k] : -1;
+#pragma unroll
+      for (int k = 0; k < kSeqChunk; ++k) {
+        if (w[k] == x) {
+          u = q0 + k;
+          ++nx;
+        }
       }
     }
     bool fast = nx == 1 && !rare;
@@ -457,40 +467,62 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
       l1 = n1 + 1;
       l2 = L - n1 + 1;
       int m1 = b, c1 = 1, m2 = x, c2 = 1;
-      for (int j = 0, q = u; j < L; ++j) {
-        const int o = v[q];
-        if (++q == L) q = 0;
-        if (j < n1) {
-          if (o < m1) {
-            m1 = o;
-            c1 = 1;
-            r1 = 1 + j;
-          } else if (o == m1) {
-            ++c1;
+      for (int j0 = 0; j0 < L; j0 += kSeqChunk) {  // v[u + j], j = 0..L-1
+        int w[kSeqChunk];
+#pragma unroll
+        for (int k = 0; k < kSeqChunk; ++k) {
+          int q = u + j0 + k;
+          if (q >= L) q -= L;
+          w[k] = (j0 + k < L) ? v[q] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kSeqChunk; ++k) {
+          const int j = j0 + k, o = w[k];
+          if (j >= L) break;
+          if (j < n1) {
+            if (o < m1) {
+              m1 = o;
+              c1 = 1;
+              r1 = 1 + j;
+            } else if (o == m1) {
+              ++c1;
+            }
+          } else if (o < m2) {
+            m2 = o;
+            c2 = 1;
+            r2 = 1 + j - n1;
+          } else if (o == m2) {
+            ++c2;
           }
-        } else if (o < m2) {
-          m2 = o;
-          c2 = 1;
-          r2 = 1 + j - n1;
-        } else if (o == m2) {
-          ++c2;
         }
       }
       fast = c1 == 1 && c2 == 1;
       if (fast) {
-        int k = r1;
-        for (int q = 0; q < l1; ++q) {  // index k >= 1: v[u + k - 1]
-          int z = u + k - 1;
-          if (z >= L) z -= L;
-          out[q] = k ? v[z] : b;
-          if (++k == l1) k = 0;
-        }
-        k = r2;
-        for (int q = 0; q < l2; ++q) {  // index k >= 1: v[t + k]
-          int z = t + k;
-          if (z >= L) z -= L;
-          out[l1 + q] = k ? v[z] : x;
-          if (++k == l2) k = 0;
+        // piece 1: index k >= 1 is v[u + k - 1]; piece 2: index k >= 1 is v[t + k]
+        for (int q0 = 0; q0 < l1 + l2; q0 += kSeqChunk) {
+          int w[kSeqChunk];
+#pragma unroll
+          for (int c = 0; c < kSeqChunk; ++c) {
+            const int q = q0 + c;
+            int val = 0;
+            if (q < l1) {
+              int k = r1 + q;
+              if (k >= l1) k -= l1;
+              int z = u + k - 1;
+              if (z >= L) z -= L;
+              val = k ? v[z] : b;
+            } else if (q < l1 + l2) {
+              int k = r2 + (q - l1);
+              if (k >= l2) k -= l2;
+              int z = t + k;
+              if (z >= L) z -= L;
+              val = k ? v[z] : x;
+            }
+            w[c] = val;
+          }
+#pragma unroll
+          for (int c = 0; c < kSeqChunk; ++c)
+            if (q0 + c < l1 + l2) out[q0 + c] = w[c];
         }
       }
     }
