@@ -436,8 +436,7 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
     }));
     POLY_TRY(launch(h, "repair_one", s, [&] {
       return launch_repair_one(M, h->lab, h->tf, h->succ, h->P, h->F, h->pool, h->Dl,
-                               h->rare_paths, h->C,
-                               h->sms, s);
+                               h->rare_paths, h->C, h->sms, s, !h->timing);
     }));
   }
   if (fork) {

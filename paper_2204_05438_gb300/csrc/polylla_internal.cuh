@@ -305,7 +305,7 @@ cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* 
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                               const LongList& D1, int rare, Counters* C, int sms,
-                              cudaStream_t s);
+                              cudaStream_t s, bool pdl);
 cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                                 const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                                 const LongList& Dm, int rare, Counters* C, int sms,

@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(kBlock) k_repair_one(DevMesh M, uint8_t* lab, 
                                                        const int* __restrict__ succ, PolyArrays P,
                                                        FinalPieces F, Pool pool, LongList D1,
                                                        int rare, Counters* C) {
+  pdl_wait();  // the walk's lists, records and sequences
   const long long nd = min(C->n_defer, D1.cap);
   const int H = (int)(3 * M.m);
   const long long limit = 3 * M.m + 3;
@@ -685,11 +686,19 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
       bool bad = false;
       if (rec) {  // the walk's records
         const int* rv = pool.v + off;
-        for (int j = 0; j < L; ++j) {
-          NH(j) = kSuccMask;
-          NO(j) = rv[j];
-          NX(j) = (uint8_t)(j + 1 == L ? 0 : j + 1);
-          PV(j) = (uint8_t)(j == 0 ? L - 1 : j - 1);
+        for (int j0 = 0; j0 < L; j0 += kSeqChunk) {
+          int w[kSeqChunk];
+#pragma unroll
+          for (int k = 0; k < kSeqChunk; ++k) w[k] = (j0 + k < L) ? rv[j0 + k] : 0;
+#pragma unroll
+          for (int k = 0; k < kSeqChunk; ++k) {
+            const int j = j0 + k;
+            if (j >= L) break;
+            NH(j) = kSuccMask;
+            NO(j) = w[k];
+            NX(j) = (uint8_t)(j + 1 == L ? 0 : j + 1);
+            PV(j) = (uint8_t)(j == 0 ? L - 1 : j - 1);
+          }
         }
         for (int k = 0; k < nt; ++k) {
           const int ix = rv[L + 2 * k], hh = rv[L + 2 * k + 1];
@@ -892,12 +901,12 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
 cudaError_t launch_repair_one(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
                               const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                               const LongList& D1, int rare, Counters* C, int sms,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool pdl) {
   static std::atomic<int> cap{0};
   const int grid = resident_grid(reinterpret_cast<const void*>(k_repair_one), kBlock, 0,
                                  (long long)sms * 8, &cap);
-  k_repair_one<<<grid, kBlock, 0, s>>>(M, lab, tf, succ, P, F, pool, D1, rare, C);
-  return cudaGetLastError();
+  return launch_chain(k_repair_one, grid, kBlock, 0, s, pdl, M, lab, tf, succ, P, F, pool, D1, rare,
+                      C);
 }
 
 cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const int* succ,
