@@ -300,8 +300,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
           } else if (x[k] >= H) {
             s_ovf[c] = 2;
           } else if (k != up) {
+            const int nb = x[k] / 3;
+            // the child's tf words and label byte to L1 now: the next level reads them
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(tf + 3 * nb));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(lab + nb));
             const int p = hi + atomicAdd(&s_cnt[c], 1);
-            if (p < kLT) RQ[p] = x[k] / 3;
+            if (p < kLT) RQ[p] = nb;
             else s_ovf[c] = 1;
           }
         }
