@@ -90,9 +90,10 @@ __device__ void block_min_key(unsigned long long key, int idx, unsigned long lon
   __syncthreads();
 }
 
-// Exclusive prefix sum of v over the block in thread order; *total gets the sum.
-// Every thread of the block calls it; s_wsum holds 33 ints.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* s_wsum, int* total) {
+// Exclusive prefix sum of v over the block in thread order, for any block size
+// (the shared helper assumes kBlock threads); *total gets the sum.  Every thread
+// of the block calls it; s_wsum holds 33 ints.
+__device__ __forceinline__ int block_scan_any(int v, int* s_wsum, int* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (int)(blockDim.x >> 5);
   int incl = v;
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_long(DevMesh M, uint8_t* lab, in
         if (name < L || name >= N) s_fail = 1;
         mine += name == L + q;
       }
-      int id = block_exclusive_scan(mine, s_wsum, &npieces);
+      int id = block_scan_any(mine, s_wsum, &npieces);
       for (int q = q0; q < q1; ++q) {
         if (B[A[L + q]] == L + q) {
           nodeof[q] = id;
