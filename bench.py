@@ -319,6 +319,14 @@ def run_ours(args, dist: Dist) -> dict | None:
     ls_ms = sum(kernels[k]["ms"] for k in label_seed)
     ls_bytes = sum(kernels[k]["alg_bytes"] for k in label_seed)
     ls_io = 24 * m + 16 * n + m + 4 * sizes["ns"]
+    # traversal: the successor pass and the walk together, against their own
+    # algorithmic bytes and against the survey's estimate of the traversal phase's
+    # bytes (about 35 B per triangle: twin, label and origin reads over the visited
+    # half-edges, the vertex and offset writes)
+    trav = [k for k in ("succ", "walk") if k in kernels]
+    tr_ms = sum(kernels[k]["ms"] for k in trav)
+    tr_bytes = sum(kernels[k]["alg_bytes"] for k in trav)
+    tr_survey = 35 * m
     traffic = None
     if NCU_TRAFFIC["sources"] == source_hash():
         traffic = NCU_TRAFFIC["bytes"].get(dom)
@@ -438,6 +446,10 @@ def run_ours(args, dist: Dist) -> dict | None:
                        "frac": round(ls_bytes / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None,
                        "alg_bytes_io": int(ls_io),
                        "frac_io": round(ls_io / (ls_ms * 1e-3) / 1e9 / peak, 4) if ls_ms else None},
+        "traversal": {"kernels": trav, "ms": round(tr_ms, 5), "alg_bytes": int(tr_bytes),
+                      "frac": round(tr_bytes / (tr_ms * 1e-3) / 1e9 / peak, 4) if tr_ms else None,
+                      "alg_bytes_survey": int(tr_survey),
+                      "frac_survey": round(tr_survey / (tr_ms * 1e-3) / 1e9 / peak, 4) if tr_ms else None},
         "twin_build": {"ms": round(statistics.mean(tw_ms), 5) if tw_ms else None,
                        "what": "polylla_mesh_build_twin: twin from tri on the device"},
         "lepp": {"ms": round(statistics.mean(lepp_ms), 5) if lepp_ms else None,
