@@ -246,6 +246,21 @@ def run_ours(args, dist: Dist) -> dict | None:
     launches = pg.launch_count(M.handle) - launches0
     clk = clocks.stop()
     ms_per_step, value = aggregate(dist, m, args.steps, local_ms)
+    # a mesh small enough for the one-block path: the multi-kernel path beside it
+    # (same steps, outside the timed region)
+    paths = None
+    if m <= pg.one_block_limit():
+        M.set_one_block(0)
+        for _ in range(args.warmup):
+            M.run(stream)
+        e0.record(stream)
+        for _ in range(args.steps):
+            M.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        M.set_one_block(pg.one_block_limit())
+        paths = {"one_block_ms_per_step": round(local_ms / args.steps, 5),
+                 "multi_kernel_ms_per_step": round(e0.elapsed_time(e1) / args.steps, 5)}
 
     # per-kernel durations: the same steps with events around every launch
     if args.kernel_steps <= 0:
@@ -460,6 +475,7 @@ def run_ours(args, dist: Dist) -> dict | None:
         "kernels": kernels,
         "mesh_stats": st,
         "mixed": mixed,
+        "paths": paths,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,

@@ -113,6 +113,8 @@ typedef struct {
                              chasing the successors */
   int64_t n_multi_turn;   /* pieces of several-tip polygons whose smallest vertex
                              repeats, their half-edges found by turning */
+  int64_t n_one_block;    /* polygons of a small mesh meshed, whole path, by one
+                             thread block (polylla_run; see polylla_set_one_block) */
 } polylla_stats;
 
 /*
@@ -221,8 +223,26 @@ polylla_status polylla_repair_host(polylla_mesh_t mesh, void* stream);
  * Algorithm 1 end to end: label, seeds, traversal and reparation.  The final
  * polygons and labels equal those of the four phase calls; the pre-reparation
  * CSR is not materialised.  Asynchronous.
+ *
+ * A mesh of at most polylla_set_one_block's limit of triangles (default
+ * polylla_one_block_limit() = 4096) is meshed by one launch of one thread block
+ * that holds the whole half-edge state in shared memory: Algorithm 2's labels,
+ * the Seed array, Algorithm 4's walks and Algorithm 5's splits (each polygon
+ * with tips split by the thread that walked it, smallest tip first) and the CSR,
+ * with the same results as the multi-kernel path (statistic n_one_block counts
+ * its polygons; the other per-path counters stay 0).  Larger meshes take the
+ * multi-kernel path, whose kernels each spread over the whole GPU.
  */
 polylla_status polylla_run(polylla_mesh_t mesh, void* stream);
+
+/*
+ * The largest mesh (in triangles) that polylla_run gives to the one-block path,
+ * 0 .. polylla_one_block_limit() (0: always the multi-kernel path).  Takes
+ * effect at the next polylla_run.  POLYLLA_ERR_INVALID_ARG for a null handle or
+ * a value out of range.  No device call.
+ */
+polylla_status polylla_set_one_block(polylla_mesh_t mesh, int64_t max_triangles);
+int64_t polylla_one_block_limit(void);
 
 /* Device pointer to lab[m] (valid after polylla_label; updated by repair). */
 polylla_status polylla_get_labels(polylla_mesh_t mesh, const uint8_t** d_lab);
@@ -488,10 +508,23 @@ void polylla_debug_fail_alloc(int64_t k);
  * (counted in n_one_chase), several-tip pieces ordered by (origin, half-edge) with
  * half-edges found by turning (n_multi_turn), and each split's far node found
  * through turn(oj) -- so that tests can compare those paths with the oracle on any
- * mesh.  The polygons are the same either way.  Errors: POLYLLA_ERR_INVALID_ARG
- * for a null handle.
+ * mesh.  The polygons are the same either way.  While it is on, polylla_run
+ * takes the multi-kernel path at every mesh size.  Errors:
+ * POLYLLA_ERR_INVALID_ARG for a null handle.
  */
 polylla_status polylla_debug_rare_paths(polylla_mesh_t mesh, int enable);
+
+/*
+ * Test switch (Section 3.2.3's order of splits, in the one-block path of
+ * polylla_run): with enable != 0, every polygon with tips is split piece by piece
+ * as the rule states it -- the first piece with a tip at its smallest tip, the
+ * piece re-walked after each split -- instead of all its tips in increasing
+ * order with the pieces ordered afterwards (the form the path takes when its
+ * scratch holds the polygon's lists), so that tests can compare both forms with
+ * the oracle.  The polygons are the same either way.  Errors:
+ * POLYLLA_ERR_INVALID_ARG for a null handle.
+ */
+polylla_status polylla_debug_split_by_pieces(polylla_mesh_t mesh, int enable);
 
 #ifdef __cplusplus
 }

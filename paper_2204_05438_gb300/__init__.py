@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n_seeds", "n_poly_trav", "n_vtx_trav", "n_tip_polygons", "n_tips", "n_splits",
         "n_poly", "n_vtx", "n_long", "n_long_handoff", "n_long_seq", "n_one_tip", "n_multi_tip",
-        "n_multi_seq", "n_one_chase", "n_multi_turn")]
+        "n_multi_seq", "n_one_chase", "n_multi_turn", "n_one_block")]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -134,6 +134,9 @@ def load_library(path: str | None = None):
             "polylla_server_cancel": ([vp, i64], st),
             "polylla_debug_fail_alloc": ([i64], None),
             "polylla_debug_rare_paths": ([vp, i32], st),
+            "polylla_set_one_block": ([vp, i64], st),
+            "polylla_debug_split_by_pieces": ([vp, i32], st),
+            "polylla_one_block_limit": ([], i64),
             "polylla_server_destroy": ([vp], st),
             "polylla_lepp": ([vp, vp], st),
             "polylla_mesh_build_twin": ([vp, vp], st),
@@ -556,6 +559,23 @@ def debug_rare_paths(mesh: int, enable: bool = True):
     _check(load_library().polylla_debug_rare_paths(mesh, int(enable)), "polylla_debug_rare_paths")
 
 
+def set_one_block(mesh: int, max_triangles: int):
+    """polylla_run meshes a mesh of at most max_triangles triangles in one thread
+    block (0: always the multi-kernel path)."""
+    _check(load_library().polylla_set_one_block(mesh, int(max_triangles)), "polylla_set_one_block")
+
+
+def debug_split_by_pieces(mesh: int, enable: bool = True):
+    """Test switch: the one-block path splits every polygon piece by piece (same
+    polygons; see the header)."""
+    _check(load_library().polylla_debug_split_by_pieces(mesh, int(enable)),
+           "polylla_debug_split_by_pieces")
+
+
+def one_block_limit() -> int:
+    return int(load_library().polylla_one_block_limit())
+
+
 def server_destroy(server: int):
     _check(load_library().polylla_server_destroy(server), "polylla_server_destroy")
 
@@ -587,6 +607,9 @@ class Mesh:
 
     def run(self, stream=None):
         run(self.handle, stream)
+
+    def set_one_block(self, max_triangles: int):
+        set_one_block(self.handle, max_triangles)
 
     def labels(self) -> torch.Tensor:
         return get_labels(self.handle, self.m)

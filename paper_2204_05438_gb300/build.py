@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpolylla.so")
 BUILD_DIR = os.path.join(ROOT, "_build", "polylla")
 SOURCES = ["api.cu", "label.cu", "trav.cu", "long.cu", "final.cu", "noalloc.cu", "batch.cu",
-           "serve.cu", "lepp.cu", "twin.cu", "repair_host.cpp"]
+           "serve.cu", "lepp.cu", "twin.cu", "block.cu", "repair_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

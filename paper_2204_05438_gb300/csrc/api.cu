@@ -88,6 +88,9 @@ struct polylla_mesh {
   bool overlap = true;  // the kernels after the walk on side streams
   bool rare_paths = false;  // polylla_debug_rare_paths
   int long_mode = 0;
+  // polylla_run meshes a mesh of at most this many triangles in one thread block
+  long long block_max = kBlockMeshMax;
+  int block_by_pieces = 0;  // polylla_debug_split_by_pieces
   bool lepp_valid = false;
   long long* obase = nullptr;  // batches: output index of each traversal polygon
 
@@ -454,6 +457,19 @@ polylla_status do_polygons(polylla_mesh* h, cudaStream_t s, int repair, long lon
   });
 }
 
+// The whole path in one launch of one thread block (small meshes).
+polylla_status do_block(polylla_mesh* h, cudaStream_t s) {
+  const Range range("polylla run (one block)");
+  const MeshBlockOut O{h->lab, h->seeds, h->off_final, h->vtx_final};
+  POLY_TRY(launch(h, "mesh_block", s, [&] {
+    return launch_mesh_block(h->M, O, h->block_by_pieces, h->C, s);
+  }));
+  h->phase = kRepaired;
+  h->latest_csr = 1;
+  h->lepp_valid = false;
+  return POLYLLA_OK;
+}
+
 polylla_status do_traverse(polylla_mesh* h, cudaStream_t s) {
   POLY_TRY(do_polygons(h, s, 0, h->off_trav, h->vtx_trav));
   h->phase = kTraversed;
@@ -647,6 +663,12 @@ void polylla_debug_fail_alloc(int64_t k) { g_fail_alloc.store(k > 0 ? k : 0); }
 polylla_status polylla_debug_rare_paths(polylla_mesh_t h, int enable) {
   if (!h) return POLYLLA_ERR_INVALID_ARG;
   h->rare_paths = enable != 0;
+  return POLYLLA_OK;
+}
+
+polylla_status polylla_debug_split_by_pieces(polylla_mesh_t h, int enable) {
+  if (!h) return POLYLLA_ERR_INVALID_ARG;
+  h->block_by_pieces = enable != 0;
   return POLYLLA_OK;
 }
 
@@ -874,10 +896,20 @@ polylla_status polylla_run(polylla_mesh_t h, void* stream) {
   POLY_TRY(check_handle(h));
   cudaStream_t s = (cudaStream_t)stream;
   h->last_stream = s;
+  if (h->M.m <= h->block_max && !h->rare_paths) return do_block(h, s);
   POLY_TRY(do_label(h, s));
   POLY_TRY(do_seeds(h, s));
   return do_repair(h, s);
 }
+
+polylla_status polylla_set_one_block(polylla_mesh_t h, int64_t max_tri) {
+  if (!h) return POLYLLA_ERR_INVALID_ARG;
+  if (max_tri < 0 || max_tri > kBlockMeshMax) return POLYLLA_ERR_INVALID_ARG;
+  h->block_max = max_tri;
+  return POLYLLA_OK;
+}
+
+int64_t polylla_one_block_limit(void) { return kBlockMeshMax; }
 
 polylla_status polylla_get_labels(polylla_mesh_t h, const uint8_t** d_lab) {
   POLY_TRY(check_handle(h));
@@ -946,6 +978,7 @@ polylla_status polylla_get_stats(polylla_mesh_t h, polylla_stats* out) {
     out->n_multi_seq = c.n_multi_seq;
     out->n_one_chase = c.n_one_chase;
     out->n_multi_turn = c.n_multi_turn;
+    out->n_one_block = c.n_block;
   }
   return POLYLLA_OK;
 }

@@ -216,7 +216,7 @@ __device__ void long_fallback(const DevMesh& M, uint8_t* lab, int* tf, int t0, l
     return;
   }
   const int cnt = repair_seq(M.tri, tf, lab, c, c.ntips + 1, H, limit, F.h + foff, F.pos + foff,
-                             F.len + foff, pool.v + off, off);
+                             F.len + foff, pool.v + off, off, need);
   if (cnt < 0) {
     set_error(C, POLYLLA_ERR_LIMIT, 105);
     return;

@@ -53,6 +53,7 @@ struct Counters {
   long long out_done;     // the output pass's completed look-backs (likewise)
   long long scratch0;     // scan totals that are not reported
   long long scratch1;
+  long long n_block;      // polygons meshed by the one-block path (block.cu)
   int error;              // first device error (polylla_status), 0 if none
   int err_info;
 };
@@ -340,6 +341,21 @@ cudaError_t launch_trivertex(const int* tri, long long m, long long n, int* tv, 
 // Longest-edge propagation paths: per triangle its region's seed and the path length.
 cudaError_t launch_lepp(const DevMesh& M, const uint8_t* lab, int* region, int* depth, Counters* C,
                         int grid, cudaStream_t s);
+// The whole path for one mesh of at most kBlockMeshMax triangles in one block of
+// kMeshThreads threads (block.cu): labels, seeds, walks, splits and the CSR.
+constexpr int kMeshThreads = 1024;
+constexpr long long kBlockMeshMax = 4096;
+struct MeshBlockOut {
+  uint8_t* lab;    // m label bytes (after reparation)
+  int* seeds;      // the ascending seed list
+  long long* off;  // final CSR offsets (capacity m + 1)
+  int* vtx;        // final CSR vertices (capacity 3m)
+};
+size_t mesh_block_smem(long long m);
+// by_pieces != 0: every polygon with tips is split piece by piece (the rule as
+// stated), never by the increasing-tip-order form (a test switch)
+cudaError_t launch_mesh_block(const DevMesh& M, const MeshBlockOut& O, int by_pieces,
+                              Counters* C, cudaStream_t s);
 // Batches: union ids from per-mesh local ids, and each mesh's first output polygon.
 cudaError_t launch_batch_globalize(const int* tri, const int* twin, const long long* tri_off,
                                    const long long* vtx_off, long long n_meshes, long long m,

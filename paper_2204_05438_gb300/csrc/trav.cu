@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(kRsThreads) k_repair_multi(DevMesh M, uint8_t*
       ++st_seq;
       const Cyc first{P.start[i], L, P.tip_h[i], nt, true};
       cnt = repair_seq(M.tri, tf, lab, first, nt + 1, H, limit, F.h + foff, F.pos + foff,
-                       F.len + foff, pool.v + off, off);
+                       F.len + foff, pool.v + off, off, L + 2 * nt);
     } else {
       cnt = -1;
       bool bad = false;

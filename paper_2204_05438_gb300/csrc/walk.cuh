@@ -159,10 +159,14 @@ __device__ __forceinline__ int split_edge(const int* tf, int barrier, int H) {
 // if x is a tip) and creates none, so at most ntips + 1 pieces arise.  Finished
 // pieces are written from their canonical start into out[], in order; piece j gets
 // (pool position pos[j], length len[j]).  `first` is the walk of the whole
-// polygon.  Returns the number of pieces, or -1 on an error.
+// polygon.  out[] holds out_cap entries (the polygon's length plus two per tip
+// suffices for a valid mesh; a corrupt one may walk longer pieces, which end the
+// split with an error instead of writing past it).  Returns the number of
+// pieces, or -1 on an error.
 __device__ __forceinline__ int repair_seq(const int* __restrict__ tri, int* tf, uint8_t* lab,
                                           Cyc first, int cap, int H, long long limit, int* ps,
-                                          long long* pos, int* plen, int* out, long long out0) {
+                                          long long* pos, int* plen, int* out, long long out0,
+                                          long long out_cap) {
   int count = 1;
   ps[0] = first.start;
   Cyc cur = first;
@@ -176,6 +180,7 @@ __device__ __forceinline__ int repair_seq(const int* __restrict__ tri, int* tf, 
     }
     known = false;
     if (cur.tip_h < 0) {
+      if (acc + cur.len > out_cap) return -1;
       if (!write_tf(tri, tf, cur.start, cur.len, H, limit, out + acc)) return -1;
       pos[j] = out0 + acc;
       plen[j] = cur.len;

@@ -260,12 +260,15 @@ def test_phase_order_is_enforced():
 
 def test_launch_count_and_timing():
     M = pg.from_numpy(meshgen.load("uniform-1k"))
-    before = pg.launch_count(M.handle)
     pg.set_timing(M.handle, True)
-    M.run()
-    times = pg.kernel_times(M.handle)
-    assert pg.launch_count(M.handle) - before == len(times) >= 6
-    assert all(ms >= 0 for _, ms in times)
+    for one_block, launches in ((0, 6), (pg.one_block_limit(), 1)):
+        M.set_one_block(one_block)
+        before = pg.launch_count(M.handle)
+        M.run()
+        times = pg.kernel_times(M.handle, reset=True)
+        assert pg.launch_count(M.handle) - before == len(times) >= launches
+        assert all(ms >= 0 for _, ms in times)
+    assert [k for k, _ in times] == ["mesh_block"]
     M.close()
 
 
