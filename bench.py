@@ -43,10 +43,11 @@ UNIT = "triangles/s"
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# on the gmm16-10m workload, keyed by the hash of the device code they were taken
-# with (source_hash); reported as null once that code changes.
+# on the gmm16-10m workload, keyed by the hash of the files that define these kernels
+# (source_hash(TRAFFIC_FILES)); reported as null once that code changes.
+TRAFFIC_FILES = ("final.cu", "label.cu", "long.cu", "polylla_internal.cuh", "trav.cu", "walk.cuh")
 NCU_TRAFFIC = {
-    "sources": "8b3871b545ae73d7",
+    "sources": "ae396f6b77e48a95",
     # one ncu --set full capture per kernel on gmm16-5m (9,999,947 triangles),
     # scaled x2.0000 by triangle count to a gmm16-10m launch
     "bytes": {"walk": int((311.452928 + 70.603520) * 1e6 * 19999948 / 9999947),
@@ -61,15 +62,17 @@ NCU_TRAFFIC = {
 
 
 # ------------------------------------------------------------------ helpers
-def source_hash() -> str:
+def source_hash(files=None) -> str:
     """Hash of the CUDA sources that hold device code (files with __global__ or
-    __device__ functions): the kernels the ncu counters were taken on.  Host-only
-    files (the C-ABI entry points, the server) do not change it, and neither do
-    comments (// to the end of a line and /* ... */ are left out) or the layout
-    of white space."""
+    __device__ functions; only `files` when given): the kernels the ncu counters
+    were taken on.  Host-only files (the C-ABI entry points, the server) do not
+    change it, and neither do comments (// to the end of a line and /* ... */ are
+    left out) or the layout of white space."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2204_05438_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
+        if files is not None and f not in files:
+            continue
         with open(os.path.join(csrc, f), "rb") as fh:
             data = fh.read()
         if b"__global__" not in data and b"__device__" not in data:
@@ -343,7 +346,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     tr_bytes = sum(kernels[k]["alg_bytes"] for k in trav)
     tr_survey = 35 * m
     traffic = None
-    if NCU_TRAFFIC["sources"] == source_hash():
+    if NCU_TRAFFIC["sources"] == source_hash(TRAFFIC_FILES):
         traffic = NCU_TRAFFIC["bytes"].get(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["gbs"], "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
@@ -588,13 +591,20 @@ def run_served(args, dist: Dist) -> dict | None:
     # before the timed window (a pinned allocation during it stalls the device)
     for j in range(len(pool)):
         free[j] = [outbuf(j) for _ in range(4)]
-    # warm the slots of every size class once (allocation is not part of serving)
-    for j in range(len(pool)):
-        S.submit(*host[j], *outbuf(j))
-    t_end = time.time() + 120
-    done = 0
-    while done < len(pool) and time.time() < t_end:
-        done += len(S.poll(wait_us=20000))
+    # warm the slots of every size class (allocation is not part of serving): each
+    # mesh once, then every mesh twice at once, so that the bursts of the timed
+    # streams find idle slots instead of creating them (a slot's allocations stall
+    # the device while the worker holds the queue)
+    for burst in (1, 2):
+        warm = [outbuf(j) for j in range(len(pool)) for _ in range(burst)]
+        for k, bufs in enumerate(warm):
+            S.submit(*host[k // burst], *bufs)
+        t_end = time.time() + 120
+        done = 0
+        while done < len(warm) and time.time() < t_end:
+            done += len(S.poll(wait_us=20000))
+        for k, bufs in enumerate(warm):
+            free[k // burst].append(bufs)
     def poisson(n_req, seed):
         """Submit n_req requests at Poisson arrivals; returns (latencies, triangles
         done, failures, first submission, last completion) once all completed."""
@@ -629,6 +639,7 @@ def run_served(args, dist: Dist) -> dict | None:
     # one untimed second of the same stream first: the slots its bursts need are
     # created before the timed window (a slot's allocation stalls the device)
     poisson(int(args.serve_rate), 1077 + dist.rank)
+    slots_before = S.info()["slots"]
     n_req = int(args.serve_rate * args.serve_seconds)
     # the tail varies from stream to stream: several independent timed streams,
     # reported as the median with the spread
@@ -658,6 +669,7 @@ def run_served(args, dist: Dist) -> dict | None:
             "failed": int(sum(t["failed"] for t in trials)),
             "per_trial": trials,
             "peak_running": info["peak_running"], "slots": info["slots"],
+            "slots_created_in_timed_streams": info["slots"] - slots_before,
             "budget_gb": args.serve_budget_gb,
             "latency": "completion minus submission, seconds on the server's steady clock; "
                        "median over the trials"}

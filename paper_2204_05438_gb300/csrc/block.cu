@@ -97,14 +97,18 @@ __device__ __forceinline__ long long sqlen(longlong2 p, longlong2 q) {
 //   polygons with tips uint16[m]: their seed indices, for the split pass
 //   split scratch      uint16[kSplitScratch]: tip lists and piece trees of the
 //                      polygons split in increasing tip order
+//   tip list           uint16[kTipList] x 2: (seed, barrier half-edge) of every tip
+//                      the walks met
 constexpr long long kPieceSlack = 4;
-constexpr int kSplitScratch = 16384;
+constexpr int kSplitScratch = 8192;
+constexpr int kTipList = 4096;
 size_t mesh_block_smem(long long m) {
   const long long m4 = (m + 3) & ~3ll;
   const long long h2 = (3 * m + 1) & ~1ll;  // uint16 arrays padded to 4 bytes
   const long long m2 = (m + 1) & ~1ll;
   const long long p2 = (2 * m + kPieceSlack + 1) & ~1ll;
-  return (size_t)(4 * 6 * m + 2 * h2 + 2 * m4 + 2 * 4 * m2 + 2 * 2 * p2 + 2 * kSplitScratch);
+  return (size_t)(4 * 6 * m + 2 * h2 + 2 * m4 + 2 * 4 * m2 + 2 * 2 * p2 + 2 * kSplitScratch +
+                  2 * 2 * kTipList);
 }
 
 namespace {
@@ -137,8 +141,12 @@ struct Piece {
 };
 
 // One cycle of the successor array from h0: its canonical start, length and
-// smallest tip (tips flagged in succ).
-__device__ __forceinline__ Piece chase(const int* tri, const uint16_t* succ, int h0, int H) {
+// smallest tip (tips flagged in succ).  With tl_n, every tip's barrier half-edge
+// is also appended with `seed` to the list tl_seed / tl_h (kTipList entries; the
+// count goes on past a full list, whose polygons are then split without it).
+__device__ __forceinline__ Piece chase(const int* tri, const uint16_t* succ, int h0, int H,
+                                       int seed = 0, uint16_t* tl_seed = nullptr,
+                                       uint16_t* tl_h = nullptr, int* tl_n = nullptr) {
   Piece p{h0, 0, -1, 0, false};
   unsigned long long best = ~0ull;
   int tipv = 0x7fffffff;
@@ -152,6 +160,13 @@ __device__ __forceinline__ Piece chase(const int* tri, const uint16_t* succ, int
     if (g >= H) return p;
     if (sg & kSuccTip) {
       ++p.ntips;
+      if (tl_n) {
+        const int j = atomicAdd(tl_n, 1);
+        if (j < kTipList) {
+          tl_seed[j] = (uint16_t)seed;
+          tl_h[j] = (uint16_t)h;
+        }
+      }
       const int b = tri[g];  // dest(h) = origin of its successor twin(h)
       if (b < tipv) {
         tipv = b;
@@ -166,16 +181,15 @@ __device__ __forceinline__ Piece chase(const int* tri, const uint16_t* succ, int
   return p;
 }
 
-// The split of tip p = a->b (Section 3.2.3) on the successor array: along
-// oj = b->x, the middle internal edge of b's fan (tw = x->b), with q = turn(oj)
-// and pq the frontier half-edge whose turn was q; p -> oj -> q and
+// The split of tip p = a->b (Section 3.2.3) on the successor array along its
+// split edge oj = b->x (the middle internal edge of b's fan; tw = x->b), with
+// q = turn(oj) and pq the frontier half-edge whose turn was q: p -> oj -> q and
 // pq -> tw -> twin(p) afterwards.  A tip flag on pq (x was a tip) drops with the
 // rewrite; split-edge marks stay.  Returns oj, or -1 on a bound violation.
-__device__ __forceinline__ int split_tip(const int* tri, int* tf, uint8_t* lab, uint16_t* succ,
-                                         int p, int H, long long limit, int* tw_out) {
+__device__ __forceinline__ int apply_split(int* tf, uint8_t* lab, uint16_t* succ, int p, int oj,
+                                           int H, long long limit) {
   const int pn = (int)(succ[p] & kSuccVal);  // twin(p) = b->a
-  const int oj = split_edge(tf, p, H);
-  if (oj < 0 || pn >= H) return -1;
+  if (oj < 0 || oj >= H || pn >= H) return -1;
   const int tw = tf_twin(tf[oj]);
   if (tw >= H) return -1;
   long long steps = 0;
@@ -188,28 +202,23 @@ __device__ __forceinline__ int split_tip(const int* tri, int* tf, uint8_t* lab, 
   succ[oj] = (uint16_t)(q | kSuccChord);
   succ[pq] = (uint16_t)(tw | (succ[pq] & kSuccChord));
   succ[tw] = (uint16_t)(pn | kSuccChord);
-  *tw_out = tw;
   return oj;
 }
 
-// Reparation of one polygon by its thread, as the sequential rule does it: the
+// Reparation of one polygon by one thread, as the sequential rule does it: the
 // pieces are listed in order, and the first piece with a tip is split at its
 // smallest tip and replaced by the piece through oj followed by the piece
 // through tw, until no piece has a tip.  Each split re-walks the piece it splits.
 // Pieces go to ps[0 .. cap) / pl[]; returns their number, or -1.
-__device__ int repair_by_pieces(const int* tri, int* tf, uint8_t* lab, uint16_t* succ, Piece c,
+__device__ int repair_by_pieces(const int* tri, int* tf, uint8_t* lab, uint16_t* succ, int start,
                                 int cap, int H, long long limit, uint16_t* ps, uint16_t* pl,
                                 long long* total) {
   int count = 1, j = 0;
-  ps[0] = (uint16_t)c.start;
-  bool known = true;  // c describes piece 0
+  ps[0] = (uint16_t)start;
   *total = 0;
   while (j < count) {
-    if (!known) {
-      c = chase(tri, succ, ps[j], H);
-      if (!c.ok) return -1;
-    }
-    known = false;
+    const Piece c = chase(tri, succ, ps[j], H);
+    if (!c.ok) return -1;
     if (c.tip < 0) {
       ps[j] = (uint16_t)c.start;
       pl[j] = (uint16_t)c.len;
@@ -218,136 +227,225 @@ __device__ int repair_by_pieces(const int* tri, int* tf, uint8_t* lab, uint16_t*
       continue;
     }
     if (count + 1 > cap) return -1;
-    int tw;
-    const int oj = split_tip(tri, tf, lab, succ, c.tip, H, limit, &tw);
+    const int oj = apply_split(tf, lab, succ, c.tip, split_edge(tf, c.tip, H), H, limit);
     if (oj < 0) return -1;
     for (int r = count; r > j + 1; --r) ps[r] = ps[r - 1];
     ps[j] = (uint16_t)oj;
-    ps[j + 1] = (uint16_t)tw;
+    ps[j + 1] = (uint16_t)tf_twin(tf[oj]);
     ++count;
   }
   return count;
 }
 
-// The same reparation without re-walking a piece per split.  Within one piece
-// the rule splits tips in increasing vertex order; a split only changes its own
-// tip's fan and cancels x if x is a tip of the same piece, and tips of different
-// pieces never meet, so splitting all of the polygon's tips in increasing order
-// (skipping those a smaller tip's split edge cancelled) makes the same split
-// edges.  The pieces are then the cycles of the successor array; the rule emits
-// them as a tree of splits (the smallest tip's split at the root, the piece
-// through oj on the left), rebuilt by joining the two sides of each split in
-// decreasing tip order.  Scratch (9 ntips + 4 entries at sc): tip barrier
-// half-edges sorted by tip vertex, their split edges and the pieces on either
-// side; per piece its group's parent, head and tail and the next piece.
-__device__ int repair_by_tips(const int* tri, int* tf, uint8_t* lab, uint16_t* succ, Piece c,
-                              int cap, int H, long long limit, uint16_t* ps, uint16_t* pl,
-                              uint16_t* sc, long long* total) {
-  const int nt = c.ntips;
+// The same reparation by the 32 lanes of a warp, without re-walking a piece per
+// split.  Within one piece the rule splits tips in increasing vertex order; a
+// split only changes its own tip's fan and cancels x if x is a tip of the same
+// piece, and tips of different pieces never meet, so splitting all of the
+// polygon's tips in increasing order (skipping those a smaller tip's split edge
+// cancelled) makes the same split edges.  A tip's fan changes only by a split
+// edge that ends at the tip, which cancels it, so every tip's split edge is found
+// at once from the labels before any split (a lane per tip); the splits are then
+// applied in order by one lane.  The pieces are the cycles of the successor
+// array: a lane per side of each split edge walks its piece, which is named by
+// its smallest split half-edge, and the lane that started there records it.  The
+// rule emits the pieces as a tree of splits (the smallest tip's split at the
+// root, the piece through oj on the left), rebuilt by joining the two sides of
+// each split in decreasing tip order.  The polygon's tips come from the list the
+// walks made (tl_seed / tl_h, ntl entries).  Scratch (13 nt + 4 (nt + 1)
+// entries at sc): the tips sorted by tip vertex, their split edges (oj, tw), the
+// pieces on either side, per side its piece's name, number, canonical start and
+// length, per piece its group's parent, head and tail and the next piece.  Every lane of the warp calls it and
+// gets the same result: the number of pieces, -1 on an error, or -2 when the
+// list lacks some of the polygon's tips (nothing changed yet).
+__device__ int repair_by_tips_warp(const int* tri, int* tf, uint8_t* lab, uint16_t* succ, int seed,
+                                   int nt, int H, long long limit, const uint16_t* tl_seed,
+                                   const uint16_t* tl_h, int ntl, uint16_t* ps, uint16_t* pl,
+                                   uint16_t* sc, long long* total) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int cap = nt + 1;
   uint16_t* tp = sc;            // barrier half-edge a->b of each tip, by increasing b
   uint16_t* toj = tp + nt;      // its split edge oj, or kNone if cancelled
   uint16_t* ttw = toj + nt;     // tw
   uint16_t* tpo = ttw + nt;     // the piece through oj, through tw
   uint16_t* tpt = tpo + nt;
-  uint16_t* upar = tpt + nt;    // per piece (cap of them): group parent
+  uint16_t* sname = tpt + nt;   // per side 2k + d: its piece's smallest split half-edge
+  uint16_t* snum = sname + 2 * nt;  // per side: its piece's number
+  uint16_t* sstart = snum + 2 * nt;  // per side: its piece's canonical start, length
+  uint16_t* slen = sstart + 2 * nt;
+  uint16_t* upar = slen + 2 * nt;   // per piece: group parent, head, tail, next
   uint16_t* uhead = upar + cap;
   uint16_t* utail = uhead + cap;
   uint16_t* unext = utail + cap;
-  // the tips, sorted by tip vertex (insertion sort; a handful per polygon)
-  int k = 0;
-  {
-    int h = c.start, steps = 0;
-    do {
-      const unsigned sg = succ[h];
-      if (sg & kSuccTip) {
-        if (k >= nt) return -1;
-        const int b = tri[he_next(h)];
-        int r = k++;
-        while (r > 0 && tri[he_next(tp[r - 1])] > b) {
-          tp[r] = tp[r - 1];
-          --r;
-        }
-        tp[r] = (uint16_t)h;
-      }
-      h = (int)(sg & kSuccVal);
-      if (h >= H || ++steps > H) return -1;
-    } while (h != c.start);
+  // the polygon's tips from the walks' list, then sorted by tip vertex (ranks)
+  uint16_t* raw = sname;
+  int got = 0;
+  for (int j0 = 0; j0 < ntl; j0 += 32) {
+    const int j = j0 + lane;
+    const bool mine = j < ntl && tl_seed[j] == seed;
+    const unsigned b = __ballot_sync(full, mine);
+    if (mine) {
+      const int pos = got + __popc(b & ((1u << lane) - 1u));
+      if (pos < nt) raw[pos] = tl_h[j];
+    }
+    got += __popc(b);
   }
-  if (k != nt) return -1;
-  int splits = 0;
-  for (k = 0; k < nt; ++k) {
-    toj[k] = (uint16_t)kNone;
+  for (int k = lane; k < nt; k += 32) tp[k] = (uint16_t)kNone;
+  __syncwarp();
+  if (got != nt) return -2;
+  for (int k = lane; k < nt; k += 32) {
+    const int h = raw[k];
+    const int b = tri[he_next(h)];
+    int rank = 0;
+    for (int r = 0; r < nt; ++r) rank += tri[he_next(raw[r])] < b;
+    tp[rank] = (uint16_t)h;
+  }
+  __syncwarp();
+  // every tip's split edge, from the labels as they are (a tip vertex met twice,
+  // on a corrupt mesh, leaves a rank empty)
+  for (int k = lane; k < nt; k += 32) {
+    const int oj = tp[k] < H ? split_edge(tf, tp[k], H) : -1;
+    toj[k] = (uint16_t)(oj < 0 ? kNone : oj);
     tpo[k] = tpt[k] = (uint16_t)kNone;
-    const int p = tp[k];
-    if (!(succ[p] & kSuccTip)) continue;  // cancelled by a smaller tip's split edge
-    int tw;
-    const int oj = split_tip(tri, tf, lab, succ, p, H, limit, &tw);
-    if (oj < 0) return -1;
-    toj[k] = (uint16_t)oj;
-    ttw[k] = (uint16_t)tw;
-    ++splits;
   }
-  if (splits + 1 > cap) return -1;
-  // the pieces: every one borders a split edge
-  int np = 0;
-  *total = 0;
-  for (k = 0; k < nt; ++k) {
-    if (toj[k] == kNone) continue;
-    for (int side = 0; side < 2; ++side) {
-      if ((side ? tpt[k] : tpo[k]) != kNone) continue;
-      if (np >= cap) return -1;
-      const int h0 = side ? ttw[k] : toj[k];
-      unsigned long long best = ~0ull;
-      int h = h0, len = 0;
-      do {
-        const unsigned sg = succ[h];
-        const unsigned long long key =
-            ((unsigned long long)(unsigned)tri[h] << 32) | (unsigned)h;
-        if (key < best) best = key;
-        if (sg & kSuccChord) {
-          for (int r = 0; r < nt; ++r) {
-            if (toj[r] == h) tpo[r] = (uint16_t)np;
-            else if (toj[r] != kNone && ttw[r] == h) tpt[r] = (uint16_t)np;
-          }
-        }
-        h = (int)(sg & kSuccVal);
-        if (h >= H || ++len > H) return -1;
-      } while (h != h0);
-      ps[np] = (uint16_t)(best & 0xffffffffu);
-      pl[np] = (uint16_t)len;
-      *total += len;
-      upar[np] = uhead[np] = utail[np] = (uint16_t)np;
-      unext[np] = (uint16_t)kNone;
-      ++np;
+  __syncwarp();
+  // the splits, in increasing tip order, by one lane
+  int splits = 0, bad = 0;
+  if (lane == 0) {
+    for (int k = 0; k < nt; ++k) {
+      const int p = tp[k];
+      if (p >= H) {
+        bad = 1;
+        break;
+      }
+      if (!(succ[p] & kSuccTip)) {  // cancelled by a smaller tip's split edge
+        toj[k] = (uint16_t)kNone;
+        continue;
+      }
+      const int oj = toj[k] == kNone ? -1 : (int)toj[k];
+      if (apply_split(tf, lab, succ, p, oj, H, limit) < 0) {
+        bad = 1;
+        break;
+      }
+      ttw[k] = (uint16_t)tf_twin(tf[oj]);
+      ++splits;
     }
   }
+  splits = __shfl_sync(full, splits, 0);
+  if (__shfl_sync(full, bad, 0) || splits + 1 > cap) return -1;
+  __syncwarp();
+  // the pieces: a lane per side of each split edge
+  const int ns2 = 2 * nt;
+  for (int s0 = 0; s0 < ns2; s0 += 32) {
+    const int sd = s0 + lane;
+    const bool live = sd < ns2 && toj[sd >> 1] != kNone;
+    int h0 = 0, name = 0x7fffffff, len = 0;
+    if (live) {
+      h0 = (sd & 1) ? ttw[sd >> 1] : toj[sd >> 1];
+      unsigned long long best = ~0ull;
+      int h = h0;
+      do {
+        const unsigned sg = succ[h];
+        const unsigned long long key = ((unsigned long long)(unsigned)tri[h] << 32) | (unsigned)h;
+        if (key < best) best = key;
+        if ((sg & kSuccChord) && h < name) name = h;
+        h = (int)(sg & kSuccVal);
+        if (h >= H || ++len > H) {
+          name = -1;
+          break;
+        }
+      } while (h != h0);
+      sname[sd] = (uint16_t)(name < 0 ? kNone : name);
+      sstart[sd] = (uint16_t)(best & 0xffffffffu);
+      slen[sd] = (uint16_t)len;
+    }
+    if (__any_sync(full, live && name < 0)) return -1;
+  }
+  __syncwarp();
+  // the lanes whose side names its piece number the pieces and record them
+  int np = 0;
+  long long tot = 0;
+  for (int s0 = 0; s0 < ns2; s0 += 32) {
+    const int sd = s0 + lane;
+    const bool live = sd < ns2 && toj[sd >> 1] != kNone;
+    const int h0 = live ? ((sd & 1) ? ttw[sd >> 1] : toj[sd >> 1]) : 0;
+    const bool owner = live && sname[sd] == h0;
+    const unsigned b = __ballot_sync(full, owner);
+    if (owner) {
+      const int num = np + __popc(b & ((1u << lane) - 1u));
+      snum[sd] = (uint16_t)num;
+      if (num < cap) {
+        ps[num] = sstart[sd];
+        pl[num] = slen[sd];
+        tot += slen[sd];
+        upar[num] = uhead[num] = utail[num] = (uint16_t)num;
+        unext[num] = (uint16_t)kNone;
+      }
+    }
+    np += __popc(b);
+  }
   if (np != splits + 1) return -1;
+  __syncwarp();
+  // every side's piece number, from the side that names its piece
+  for (int sd = lane; sd < ns2; sd += 32) {
+    if (toj[sd >> 1] == kNone) continue;
+    const int name = sname[sd];
+    int num = kNone;
+    for (int r = 0; r < ns2; ++r) {
+      if (toj[r >> 1] == kNone) continue;
+      if (((r & 1) ? ttw[r >> 1] : toj[r >> 1]) == name) {
+        num = snum[r];
+        break;
+      }
+    }
+    if (sd & 1) tpt[sd >> 1] = (uint16_t)num;
+    else tpo[sd >> 1] = (uint16_t)num;
+  }
+  __syncwarp();
   // the split tree: the two sides of each split joined, largest tip first
-  for (k = nt - 1; k >= 0; --k) {
-    if (toj[k] == kNone) continue;
-    int a = tpo[k], b = tpt[k];
-    if (a >= np || b >= np) return -1;
-    while (upar[a] != a) a = upar[a];  // a forest: each join hangs one root under another
-    while (upar[b] != b) b = upar[b];
-    if (a == b) return -1;
-    unext[utail[a]] = uhead[b];
-    utail[a] = utail[b];
-    upar[b] = (uint16_t)a;
+  for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(full, tot, d);
+  *total = tot;
+  int ok = 1;
+  if (lane == 0) {
+    for (int k = nt - 1; k >= 0 && ok; --k) {
+      if (toj[k] == kNone) continue;
+      int a = tpo[k], b = tpt[k];
+      if (a >= np || b >= np) {
+        ok = 0;
+        break;
+      }
+      while (upar[a] != a) a = upar[a];  // a forest: each join hangs one root under another
+      while (upar[b] != b) b = upar[b];
+      if (a == b) {
+        ok = 0;
+        break;
+      }
+      unext[utail[a]] = uhead[b];
+      utail[a] = utail[b];
+      upar[b] = (uint16_t)a;
+    }
+    if (ok) {
+      int r0 = 0;
+      while (upar[r0] != r0) r0 = upar[r0];
+      // the pieces in that order (the group arrays are free now)
+      for (int i = 0; i < np; ++i) {
+        upar[i] = ps[i];
+        utail[i] = pl[i];
+      }
+      for (int i = uhead[r0], j = 0; j < np; ++j) {
+        if (i == (int)kNone) {
+          ok = 0;
+          break;
+        }
+        ps[j] = upar[i];
+        pl[j] = utail[i];
+        i = unext[i];
+      }
+    }
   }
-  int r0 = 0;
-  while (upar[r0] != r0) r0 = upar[r0];
-  // the pieces in that order (the group arrays are free now)
-  for (int i = 0; i < np; ++i) {
-    upar[i] = ps[i];
-    utail[i] = pl[i];
-  }
-  for (int i = uhead[r0], j = 0; j < np; ++j) {
-    if (i == (int)kNone) return -1;
-    ps[j] = upar[i];
-    pl[j] = utail[i];
-    i = unext[i];
-  }
-  return np;
+  ok = __shfl_sync(full, ok, 0);
+  __syncwarp();
+  return ok ? np : -1;
 }
 
 }  // namespace
@@ -357,7 +455,7 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
   extern __shared__ __align__(16) int mb_smem[];
   __shared__ long long s_scan[64];
   __shared__ unsigned long long s_stat[4];  // traversal length, tips, polygons with tips, splits
-  __shared__ int s_piece, s_scratch, s_ntipped;
+  __shared__ int s_piece, s_scratch, s_ntipped, s_ntl;
   const int tid = threadIdx.x, lane = tid & 31;
   const int m = (int)M.m;
   const long long n = M.n;
@@ -378,6 +476,8 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
   uint16_t* pc_h = tipped + m2;    // piece records: start half-edge
   uint16_t* pc_len = pc_h + p2;    //                length
   uint16_t* scratch = pc_len + p2;
+  uint16_t* tl_seed = scratch + kSplitScratch;  // the tips the walks met
+  uint16_t* tl_h = tl_seed + kTipList;
 
   // this launch is the whole run: its counters start at zero, as the label
   // phase's memset leaves them for the multi-kernel path
@@ -389,6 +489,7 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
     s_piece = 0;
     s_scratch = 0;
     s_ntipped = 0;
+    s_ntl = 0;
   }
   for (int i = tid; i < H; i += kMeshThreads) {
     tri[i] = __ldg(M.tri + i);
@@ -493,8 +594,9 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
     }
   __syncthreads();
 
-  // traversal, one thread per seed: the walk follows succ; a polygon without
-  // tips is done, one with tips is listed for the split pass
+  // traversal, one thread per seed: the walk follows succ and lists the tips it
+  // meets; a polygon without tips is done, one with tips is listed for the split
+  // pass with its canonical start, length and tip count
   unsigned long long st_len = 0, st_tips = 0, st_tp = 0, st_splits = 0;
   for (int i = tid; i < (int)ns; i += kMeshThreads) {
     const int t = r_start[i];
@@ -504,7 +606,7 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
     if (e < 0) {
       set_error(C, POLYLLA_ERR_LIMIT, 143);
     } else {
-      c = chase(tri, succ, e, H);
+      c = chase(tri, succ, e, H, i, tl_seed, tl_h, &s_ntl);
       if (!c.ok) set_error(C, POLYLLA_ERR_LIMIT, 144);
     }
     if (c.ok) {
@@ -512,10 +614,11 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
       st_tips += c.ntips;
       st_tp += c.ntips > 0;
       head = c.start;
+      len = c.len;
       if (c.tip < 0) {
         cnt = 1;
-        len = c.len;
       } else {
+        cnt = c.ntips;
         tipped[atomicAdd(&s_ntipped, 1)] = (uint16_t)i;
       }
     }
@@ -525,38 +628,50 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
   }
   __syncthreads();
 
-  // reparation, one warp per polygon with tips (its first lane splits it on the
-  // successor array; only this region's half-edges change): its tips in
-  // increasing order when the scratch holds its lists, else piece by piece.
-  // One polygon per warp keeps their different control flows from serialising
-  // inside a warp.
+  // reparation, one warp per polygon with tips (only its region's half-edges
+  // change): the warp splits its tips in increasing order when the scratch and
+  // the tip list hold them, else its first lane splits it piece by piece.
   const int warp = tid >> 5;
+  const int ntl = min(s_ntl, kTipList);
   for (int k = warp; k < s_ntipped; k += kMeshThreads / 32) {
-    if (lane != 0) continue;
     const int i = tipped[k];
-    const Piece c = chase(tri, succ, r_start[i], H);
-    const int cap = c.ntips + 1;
-    const int pb = c.ok && c.tip >= 0 ? atomicAdd(&s_piece, cap) : pcap;
+    const int start = r_start[i];
+    const int nt = r_cnt[i];  // the walk's tip count
+    const int cap = nt + 1;
+    const int need = 13 * nt + 4 * cap;
+    int pb = 0, sb0 = 0;
+    if (lane == 0) {
+      pb = atomicAdd(&s_piece, cap);
+      sb0 = by_pieces ? kSplitScratch : atomicAdd(&s_scratch, need);
+    }
+    pb = __shfl_sync(0xffffffffu, pb, 0);
+    sb0 = __shfl_sync(0xffffffffu, sb0, 0);
     long long total = 0;
     int r = -1;
     if (pb + cap <= pcap) {
-      const int need = 5 * c.ntips + 4 * cap;
-      const int sb0 = c.ntips > 1 && !by_pieces ? atomicAdd(&s_scratch, need) : kSplitScratch;
-      r = sb0 + need <= kSplitScratch
-              ? repair_by_tips(tri, tf, lab, succ, c, cap, H, limit, pc_h + pb, pc_len + pb,
-                               scratch + sb0, &total)
-              : repair_by_pieces(tri, tf, lab, succ, c, cap, H, limit, pc_h + pb, pc_len + pb,
-                                 &total);
+      r = -2;
+      if (sb0 + need <= kSplitScratch)
+        r = repair_by_tips_warp(tri, tf, lab, succ, i, nt, H, limit, tl_seed, tl_h, ntl,
+                                pc_h + pb, pc_len + pb, scratch + sb0, &total);
+      if (r == -2) {
+        if (lane == 0)
+          r = repair_by_pieces(tri, tf, lab, succ, start, cap, H, limit, pc_h + pb, pc_len + pb,
+                               &total);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        total = __shfl_sync(0xffffffffu, total, 0);
+      }
     }
-    if (r < 1) {
-      set_error(C, POLYLLA_ERR_LIMIT, 146);
-      r_cnt[i] = 0;
-      r_len[i] = 0;
-    } else {
-      r_start[i] = (uint16_t)pb;
-      r_cnt[i] = (uint16_t)(r | (int)kSplitFlag);
-      r_len[i] = (uint16_t)total;
-      st_splits += r - 1;
+    if (lane == 0) {
+      if (r < 1) {
+        set_error(C, POLYLLA_ERR_LIMIT, 146);
+        r_cnt[i] = 0;
+        r_len[i] = 0;
+      } else {
+        r_start[i] = (uint16_t)pb;
+        r_cnt[i] = (uint16_t)(r | (int)kSplitFlag);
+        r_len[i] = (uint16_t)total;
+        st_splits += r - 1;
+      }
     }
   }
   // per-warp sums, one shared atomic per warp and statistic
