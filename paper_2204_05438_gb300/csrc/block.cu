@@ -102,6 +102,9 @@ __device__ __forceinline__ long long sqlen(longlong2 p, longlong2 q) {
 constexpr long long kPieceSlack = 4;
 constexpr int kSplitScratch = 8192;
 constexpr int kTipList = 4096;
+static_assert(3 * kBlockMeshMax < (1 << 14), "half-edge ids and lengths fit 14 bits");
+static_assert(2 * kBlockMeshMax + kPieceSlack < (1 << 15) && kSplitScratch < (1 << 16),
+              "piece-record and scratch positions fit 16 bits");
 size_t mesh_block_smem(long long m) {
   const long long m4 = (m + 3) & ~3ll;
   const long long h2 = (3 * m + 1) & ~1ll;  // uint16 arrays padded to 4 bytes
