@@ -109,6 +109,32 @@ def test_many_tips_on_one_polygon():
     assert ref["splits"] >= 30
 
 
+def hub_grid(count: int, cols: int = 9):
+    """`count` tip hubs side by side on a grid (coordinates stay below 2^30)."""
+    meshes = [tip_hub() for _ in range(count)]
+    xy, tri, twin, nv, nh = [], [], [], 0, 0
+    for j, mesh in enumerate(meshes):
+        xy.append(mesh["xy"] + np.array([(j % cols) << 25, (j // cols) << 25], np.int64))
+        tri.append(mesh["tri"] + nv)
+        tw = mesh["twin"].copy()
+        tw[tw >= 0] += nh
+        twin.append(tw)
+        nv += mesh["xy"].shape[0]
+        nh += 3 * mesh["tri"].shape[0]
+    return {"xy": np.concatenate(xy), "tri": np.concatenate(tri).astype(np.int32),
+            "twin": np.concatenate(twin).astype(np.int32)}
+
+
+def test_split_scratch_overflow_falls_back_to_pieces():
+    """75 tip hubs (4,050 triangles, 750 tips): their tip lists and piece trees
+    need more than the block's split scratch, so the polygons that come late split
+    piece by piece while the others split in tip order; all match the oracle."""
+    mesh = hub_grid(75)
+    assert mesh["tri"].shape[0] <= pg.one_block_limit() and mesh["xy"].max() < (1 << 30)
+    ref = check_block(mesh, runs=1)
+    assert ref["splits"] == 750
+
+
 def test_tip_order_and_repeated_vertex():
     for mesh in tip_order_meshes() + [repeated_vertex_split()]:
         check_block(mesh)
