@@ -746,14 +746,10 @@ __global__ void __launch_bounds__(kMeshThreads, 1) k_mesh_block(DevMesh M, MeshB
 cudaError_t launch_mesh_block(const DevMesh& M, const MeshBlockOut& O, int by_pieces,
                               Counters* C, cudaStream_t s) {
   if (M.m < 1 || M.m > kBlockMeshMax) return cudaErrorInvalidValue;
-  static std::atomic<bool> attr{false};
-  if (!attr.load()) {
-    const cudaError_t e = cudaFuncSetAttribute(k_mesh_block,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)mesh_block_smem(kBlockMeshMax));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<bool> attr[kMaxDevices];
+  const cudaError_t e = smem_limit_once(reinterpret_cast<const void*>(k_mesh_block),
+                                        (int)mesh_block_smem(kBlockMeshMax), attr);
+  if (e != cudaSuccess) return e;
   k_mesh_block<<<1, kMeshThreads, mesh_block_smem(M.m), s>>>(M, O, by_pieces, C);
   return cudaGetLastError();
 }

@@ -733,12 +733,10 @@ cudaError_t launch_long_t(const DevMesh& M, uint8_t* lab, int* tf, const int* se
                           const LongList& over, long long* n_over, int* loc, int* vstamp,
                           int epoch, int repair, Counters* C, int grid, cudaStream_t s) {
   const size_t smem = sizeof(int) * (size_t)long_smem_ints<LM, LT>();
-  static std::atomic<bool> attr{false};
-  if (!attr.load()) {
-    cudaFuncSetAttribute(k_long<THREADS, LM, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr = true;
-  }
+  static std::atomic<bool> attr[kMaxDevices];
+  const cudaError_t e =
+      smem_limit_once(reinterpret_cast<const void*>(k_long<THREADS, LM, LT>), (int)smem, attr);
+  if (e != cudaSuccess) return e;
   static std::atomic<int> cap{0};
   grid = resident_grid(reinterpret_cast<const void*>(k_long<THREADS, LM, LT>), THREADS, smem,
                        grid, &cap);

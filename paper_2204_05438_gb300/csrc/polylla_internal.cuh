@@ -228,6 +228,21 @@ inline int resident_grid(const void* kernel, int threads, size_t smem, long long
   return (int)(g < 1 ? 1 : g);
 }
 
+// A kernel's dynamic shared-memory limit raised to `bytes`, once per device: the
+// attribute belongs to the device's context, so a process that launches on several
+// devices sets it on each.  done: one flag per device (a launcher's static array).
+constexpr int kMaxDevices = 64;
+inline cudaError_t smem_limit_once(const void* kernel, int bytes, std::atomic<bool>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < kMaxDevices;
+  if (cached && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && cached) done[dev].store(true, std::memory_order_release);
+  return e;
+}
+
 // ----------------------------------------------------------------- launchers
 // Every launcher enqueues one kernel on `s` and returns the launch error.
 cudaError_t launch_validate(const DevMesh& M, Counters* C, int grid, cudaStream_t s);

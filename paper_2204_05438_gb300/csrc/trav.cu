@@ -367,12 +367,10 @@ cudaError_t launch_walk(const DevMesh& M, int* tf, const int* entry, const int* 
                         int tips_to_long, Counters* C, int grid, cudaStream_t s, bool pdl) {
   if (cap < 16 || cap > kWalkCap || cap % 16) return cudaErrorInvalidValue;
   const size_t smem = sizeof(int) * (size_t)kWalkThreads * cap;
-  static std::atomic<bool> attr{false};
-  if (!attr.load()) {
-    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(int) * kWalkThreads * kWalkCap));
-    attr = true;
-  }
+  static std::atomic<bool> attr[kMaxDevices];
+  const cudaError_t e = smem_limit_once(reinterpret_cast<const void*>(k_walk),
+                                        (int)(sizeof(int) * kWalkThreads * kWalkCap), attr);
+  if (e != cudaSuccess) return e;
   static std::atomic<int> resident[kWalkCap / 16 + 1] = {};
   grid = resident_grid(reinterpret_cast<const void*>(k_walk), kWalkThreads, smem, grid,
                        &resident[cap / 16]);
@@ -913,12 +911,10 @@ cudaError_t launch_repair_multi(const DevMesh& M, uint8_t* lab, int* tf, const i
                                 const PolyArrays& P, const FinalPieces& F, const Pool& pool,
                                 const LongList& Dm, int rare, Counters* C, int sms,
                                 cudaStream_t s) {
-  static std::atomic<bool> attr{false};
-  if (!attr.load()) {
-    cudaFuncSetAttribute(k_repair_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kRsSmem);
-    attr = true;
-  }
+  static std::atomic<bool> attr[kMaxDevices];
+  const cudaError_t e =
+      smem_limit_once(reinterpret_cast<const void*>(k_repair_multi), (int)kRsSmem, attr);
+  if (e != cudaSuccess) return e;
   const int per_sm = (int)((220 * 1024) / (kRsSmem + 1024));
   const int grid = sms * (per_sm < 1 ? 1 : per_sm);
   k_repair_multi<<<grid, kRsThreads, kRsSmem, s>>>(M, lab, tf, succ, P, F, pool, Dm, rare, C);
