@@ -7,9 +7,15 @@
 // buffers, output CSR -- stays allocated and is reused by the next request of
 // that class.  One worker thread:
 //   * admits pending requests in arrival order while a free slot of the right
-//     class (or of a class up to 8x larger) exists or a new one fits the budget
-//     (idle slots of other classes are released to make room); a request whose
-//     class alone exceeds the budget fails with POLYLLA_ERR_OOM;
+//     class (or of a class up to 8x larger) exists; otherwise it reserves the
+//     budget for a new slot (idle slots of other classes are released to make
+//     room) and a second thread creates it, so that the allocations never hold up
+//     the requests already on the device; a request whose class alone exceeds the
+//     budget fails with POLYLLA_ERR_OOM, and one whose slot cannot be allocated
+//     fails with POLYLLA_ERR_OOM when the creation does;
+//   * keeps one idle slot ahead of demand: when a request takes the last idle slot
+//     that could serve its class, a spare of that class is created in the
+//     background if it fits the budget and leaves one slot of the slot limit free;
 //   * runs each admitted request on its slot's stream -- host-to-device copy of
 //     the inputs, the whole path (polylla_run), a copy of the output counts --
 //     so the requests that are admitted together overlap on the device;
@@ -18,12 +24,14 @@
 // Requests that arrive while others are on the GPU are admitted as soon as a
 // slot and memory free up; each is meshed by its own handle, so its result does
 // not depend on what else is running.
+#include <algorithm>
 #include <condition_variable>
 #include <chrono>
 #include <deque>
 #include <mutex>
 #include <new>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -81,6 +89,15 @@ struct polylla_server {
   std::deque<SReq> pending;
   std::vector<polylla_result> done;
   std::vector<Slot*> slots;
+  // slot creation on the creator thread: queued and in-flight creations (size
+  // class, the request that waits for it or -1 for a spare), and the requests
+  // whose slot could not be allocated
+  std::condition_variable cv_create;
+  std::deque<std::pair<int64_t, int64_t>> to_create;
+  std::vector<std::pair<int64_t, int64_t>> creating;
+  std::vector<int64_t> create_failed;
+  std::thread creator;
+  bool creator_stop = false;  // set once the worker has finished
   int64_t used = 0;
   int64_t next_id = 1;
   int64_t completed = 0;
@@ -174,6 +191,22 @@ void fail_pending(polylla_server* S, const SReq& q, int32_t status) {
   S->done.push_back(r);
 }
 
+// An idle slot that can serve size class cls (its class up to 8x larger).
+bool idle_slot_for(const polylla_server* S, int64_t cls) {
+  for (const Slot* s : S->slots)
+    if (s->stage == 0 && s->cls >= cls && s->cls <= 8 * cls) return true;
+  return false;
+}
+
+// A queued or in-flight creation of a slot that can serve size class cls.
+bool creation_for(const polylla_server* S, int64_t cls) {
+  for (const auto& c : S->to_create)
+    if (c.first >= cls && c.first <= 8 * cls) return true;
+  for (const auto& c : S->creating)
+    if (c.first >= cls && c.first <= 8 * cls) return true;
+  return false;
+}
+
 // One pass over the slots and the queue; returns whether anything moved.
 bool step(polylla_server* S) {
   bool moved = false;
@@ -236,8 +269,22 @@ bool step(polylla_server* S) {
       if (s->stage == 0 && s->cls >= cls && s->cls <= 8 * cls && (!pick || s->cls < pick->cls))
         pick = s;
     if (!pick) {
+      // its slot could not be allocated
+      auto failed = std::find(S->create_failed.begin(), S->create_failed.end(), q.id);
+      if (failed != S->create_failed.end()) {
+        S->create_failed.erase(failed);
+        fail_pending(S, q, POLYLLA_ERR_OOM);
+        S->pending.pop_front();
+        S->cv_done.notify_all();
+        moved = true;
+        continue;
+      }
+      // a slot that can serve it is being created: wait for it
+      if (creation_for(S, cls)) break;
       // make room: release idle slots of other classes, oldest first
-      while ((S->used + need > S->budget || (int)S->slots.size() >= S->max_slots)) {
+      while ((S->used + need > S->budget ||
+              (int)(S->slots.size() + S->creating.size() + S->to_create.size()) >=
+                  S->max_slots)) {
         Slot* victim = nullptr;
         size_t vi = 0;
         for (size_t k = 0; k < S->slots.size(); ++k) {
@@ -252,17 +299,13 @@ bool step(polylla_server* S) {
         S->slots.erase(S->slots.begin() + (long)vi);
         destroy_slot(victim);
       }
-      if (S->used + need > S->budget || (int)S->slots.size() >= S->max_slots) break;  // wait
-      pick = create_slot(cls);
-      if (!pick) {
-        fail_pending(S, q, POLYLLA_ERR_OOM);
-        S->pending.pop_front();
-        S->cv_done.notify_all();
-        moved = true;
-        continue;
-      }
-      S->used += pick->bytes;
-      S->slots.push_back(pick);
+      if (S->used + need > S->budget ||
+          (int)(S->slots.size() + S->creating.size() + S->to_create.size()) >= S->max_slots)
+        break;  // wait
+      S->used += need;  // reserved for the slot the creator thread allocates
+      S->to_create.emplace_back(cls, q.id);
+      S->cv_create.notify_one();
+      break;  // wait for it
     }
     pick->req = q;
     pick->req.t_admit = S->now();
@@ -273,6 +316,13 @@ bool step(polylla_server* S) {
     const polylla_status st = start(pick, pick->req);
     if (st != POLYLLA_OK) finish(S, pick, st);
     moved = true;
+    // a spare ahead of the next burst of this class, if none is idle or coming
+    if (!idle_slot_for(S, cls) && !creation_for(S, cls) && S->used + need <= S->budget &&
+        (int)(S->slots.size() + S->creating.size() + S->to_create.size()) + 1 < S->max_slots) {
+      S->used += need;
+      S->to_create.emplace_back(cls, -1);
+      S->cv_create.notify_one();
+    }
   }
   return moved;
 }
@@ -295,10 +345,33 @@ void worker_main(polylla_server* S) {
     if (S->stop && S->pending.empty() && S->running == 0) break;
     if (!moved) S->cv_work.wait_for(lk, S->running > 0 ? kPollBusy : kPollIdle);
   }
-  for (Slot* s : S->slots) destroy_slot(s);
-  S->slots.clear();
-  S->used = 0;
   S->cv_done.notify_all();
+}
+
+// Creates the slots the worker asks for, outside the server's lock (a slot's
+// device and pinned allocations take milliseconds), and hands them over idle.
+void creator_main(polylla_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->cv_create.wait(lk, [&] { return S->creator_stop || !S->to_create.empty(); });
+    if (S->creator_stop) break;  // the worker is done: no request waits for a slot
+    const std::pair<int64_t, int64_t> job = S->to_create.front();
+    S->to_create.pop_front();
+    S->creating.push_back(job);
+    lk.unlock();
+    Slot* s = create_slot(job.first);
+    lk.lock();
+    S->creating.erase(std::find(S->creating.begin(), S->creating.end(), job));
+    if (s) {
+      s->idle_since = Clock::now();
+      S->slots.push_back(s);
+    } else {
+      S->used -= slot_bytes(job.first);
+      if (job.second >= 0) S->create_failed.push_back(job.second);
+    }
+    S->cv_work.notify_all();
+  }
 }
 
 }  // namespace
@@ -320,8 +393,20 @@ polylla_status polylla_server_create(int64_t budget_bytes, int max_slots, polyll
   S->max_slots = max_slots;
   S->t0 = Clock::now();
   try {
+    S->creator = std::thread(creator_main, S);
+  } catch (...) {
+    delete S;
+    return POLYLLA_ERR_OOM;
+  }
+  try {
     S->worker = std::thread(worker_main, S);
   } catch (...) {
+    {
+      std::lock_guard<std::mutex> g(S->mu);
+      S->creator_stop = true;
+    }
+    S->cv_create.notify_all();
+    S->creator.join();
     delete S;
     return POLYLLA_ERR_OOM;
   }
@@ -404,7 +489,16 @@ polylla_status polylla_server_destroy(polylla_server_t S) {
     S->stop = true;
   }
   S->cv_work.notify_all();
-  if (S->worker.joinable()) S->worker.join();
+  if (S->worker.joinable()) S->worker.join();  // every request completed
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->creator_stop = true;
+  }
+  S->cv_create.notify_all();
+  if (S->creator.joinable()) S->creator.join();
+  for (Slot* s : S->slots) destroy_slot(s);
+  S->slots.clear();
+  S->used = 0;
   delete S;
   return POLYLLA_OK;
 }
