@@ -437,9 +437,9 @@ polylla_status polylla_get_polygons_async(polylla_mesh_t mesh, const int64_t** d
 
 /*
  * Served form: a request loop with continuous batching (no counterpart in the
- * paper).  polylla_server_create starts a worker thread on the current device
- * with a device-memory budget (bytes, >= 1 MiB) and at most max_slots resident
- * slots.  A slot is a capacity handle for a size class (the smallest power of two
+ * paper).  polylla_server_create starts a worker thread and a slot-creating
+ * thread on the current device with a device-memory budget (bytes, >= 1 MiB) and
+ * at most max_slots resident slots.  A slot is a capacity handle for a size class (the smallest power of two
  * c >= max(4096, m, 2n) triangles, up to c/2 + 2 vertices) whose device state
  * stays allocated and serves the next request of its class, or of a smaller
  * class (up to 8x smaller) when no slot of that class is free.
@@ -449,11 +449,16 @@ polylla_status polylla_get_polygons_async(polylla_mesh_t mesh, const int64_t** d
  * returns its id.  h_off_out
  * (int64[m+1]) and h_vtx_out (int32[3m]) receive the final CSR.  Every buffer
  * must stay valid until the request completes.  Requests are admitted in arrival
- * order as soon as a slot of their class is free or a new one fits the budget
- * (idle slots of other classes are released to make room); a request whose class
- * alone exceeds the budget completes with POLYLLA_ERR_OOM.  Admitted requests run
- * on their slots' streams and overlap on the device; each is meshed by its own
- * handle, so its result is the same as alone.
+ * order as soon as a slot of their class is free; otherwise, when a new slot fits
+ * the budget (idle slots of other classes are released to make room), it is
+ * allocated by the slot-creating thread while the requests on the device go on,
+ * and the request waits for it.  When a request takes the last idle slot that can
+ * serve its class, a spare of that class is allocated the same way if it fits
+ * the budget and leaves one slot of max_slots free.  A request whose class alone
+ * exceeds the budget, or whose slot cannot be allocated, completes with
+ * POLYLLA_ERR_OOM.  Admitted requests run on their slots' streams and overlap on
+ * the device; each is meshed by its own handle, so its result is the same as
+ * alone.  bytes_in_use (polylla_server_info) counts the slots being allocated.
  *
  * polylla_server_poll moves up to `cap` completed results into out[], waiting up
  * to wait_us microseconds for the first, and returns how many (-1 on bad
