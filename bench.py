@@ -47,17 +47,17 @@ FALLBACK_HBM_GBS = 6800.0
 # (source_hash(TRAFFIC_FILES)); reported as null once that code changes.
 TRAFFIC_FILES = ("final.cu", "label.cu", "long.cu", "polylla_internal.cuh", "trav.cu", "walk.cuh")
 NCU_TRAFFIC = {
-    "sources": "ae396f6b77e48a95",
+    "sources": "fe8214375f1b7185",
     # one ncu --set full capture per kernel on gmm16-5m (9,999,947 triangles),
     # scaled x2.0000 by triangle count to a gmm16-10m launch
-    "bytes": {"walk": int((311.452928 + 70.603520) * 1e6 * 19999948 / 9999947),
-              "succ": int((232.389888 + 105.727744) * 1e6 * 19999948 / 9999947),
-              "out_write": int((90.140416 + 28.491264) * 1e6 * 19999948 / 9999947),
-              "label_class": int((130.075648 + 80.109312) * 1e6 * 19999948 / 9999947),
-              "label_max": int((200.068352 + 9.024768) * 1e6 * 19999948 / 9999947),
-              "seed_write": int((10.048000 + 0.000000) * 1e6 * 19999948 / 9999947),
-              "repair_one": int((83.737600 + 3.716864) * 1e6 * 19999948 / 9999947),
-              "repair_multi": int((15.205376 + 0.002816) * 1e6 * 19999948 / 9999947)},
+    "bytes": {"walk": int((311.370 + 70.850) * 1e6 * 19999948 / 9999947),
+              "succ": int((232.247 + 105.619) * 1e6 * 19999948 / 9999947),
+              "out_write": int((90.156 + 27.965) * 1e6 * 19999948 / 9999947),
+              "label_class": int((130.077 + 80.119) * 1e6 * 19999948 / 9999947),
+              "label_max": int((200.068 + 8.866) * 1e6 * 19999948 / 9999947),
+              "seed_write": int((10.046 + 0.001) * 1e6 * 19999948 / 9999947),
+              "repair_one": int((83.686 + 3.596) * 1e6 * 19999948 / 9999947),
+              "repair_multi": int((15.205 + 0.003) * 1e6 * 19999948 / 9999947)},
 }
 
 
