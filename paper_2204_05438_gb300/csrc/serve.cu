@@ -207,8 +207,9 @@ bool creation_for(const polylla_server* S, int64_t cls) {
   return false;
 }
 
-// One pass over the slots and the queue; returns whether anything moved.
-bool step(polylla_server* S) {
+// The requests on the device whose current stage has ended: the output copy
+// started, or the request completed.  Returns whether any moved.
+bool poll_running(polylla_server* S) {
   bool moved = false;
   for (Slot* s : S->slots) {
     if (s->stage == 0) continue;
@@ -249,7 +250,15 @@ bool step(polylla_server* S) {
     }
   }
   if (moved) S->cv_done.notify_all();
-  // admissions, in arrival order
+  return moved;
+}
+
+// One pass over the slots and the queue; returns whether anything moved.
+bool step(polylla_server* S) {
+  bool moved = poll_running(S);
+  // admissions, in arrival order; the running requests are checked again after
+  // each one (enqueuing a request takes tens of microseconds of launches, and a
+  // burst of admissions would otherwise hold up every completion behind it)
   while (!S->pending.empty()) {
     const SReq& q = S->pending.front();
     const int64_t cls = class_of(q.n, q.m);
@@ -316,6 +325,7 @@ bool step(polylla_server* S) {
     const polylla_status st = start(pick, pick->req);
     if (st != POLYLLA_OK) finish(S, pick, st);
     moved = true;
+    poll_running(S);
     // a spare ahead of the next burst of this class, if none is idle or coming
     if (!idle_slot_for(S, cls) && !creation_for(S, cls) && S->used + need <= S->budget &&
         (int)(S->slots.size() + S->creating.size() + S->to_create.size()) + 1 < S->max_slots) {
