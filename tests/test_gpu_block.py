@@ -97,6 +97,20 @@ def test_random(n, kind, seed):
     check_block(meshgen.generate(kind, n, 1 << 20, seed))
 
 
+@pytest.mark.parametrize("seed", range(40))
+def test_random_sweep(seed):
+    """Random small meshes of both kinds, 50 to 2,000 points, on lattices from 2^8
+    (many equal lengths, so the tie rule decides) to 2^22, in both split orders."""
+    rng = np.random.default_rng(7000 + seed)
+    kind = "gmm" if seed % 2 else "uniform"
+    n = int(rng.integers(50, 2001))
+    side = 1 << int(rng.integers(8, 23))
+    mesh = meshgen.generate(kind, n, side, 9000 + seed)
+    if mesh["tri"].shape[0] > pg.one_block_limit():
+        pytest.skip("larger than the one-block limit")
+    check_block(mesh)
+
+
 def test_uniform_1k():
     ref = check_block(meshgen.load("uniform-1k"))
     assert ref["splits"] > 0
