@@ -12,11 +12,14 @@
 //   Seed array, compacted           ascending, by a block scan;
 //   traversal (Algorithms 3, 4)     one thread per seed follows the successors
 //                                   around its region's boundary, noting the
-//                                   canonical start and the tips;
-//   reparation (Algorithm 5)        one warp per polygon with tips: a thread splits
-//                                   it on the successor array (split edges made
-//                                   frontier, four successors relinked per split)
-//                                   and lists its pieces in the rule's order;
+//                                   canonical start and listing the tips;
+//   reparation (Algorithm 5)        one warp per polygon with tips: the split edges
+//                                   of its tips a lane each, the splits applied in
+//                                   increasing tip order by one lane on the
+//                                   successor array (split edges made frontier,
+//                                   four successors relinked per split), the
+//                                   pieces walked a lane per split-edge side and
+//                                   listed in the rule's order;
 //   CSR output                      one block scan of (pieces, vertices) per seed,
 //                                   then every piece written from its canonical
 //                                   start along the successors.
