@@ -85,14 +85,14 @@ def source_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-L2_BYTES = 126 << 20  # the GB300's L2 as the CUDA runtime reports it
+L2_BYTES = 126 << 20  # the GB300's L2 as the CUDA runtime reports it (when no device says)
 
 
-def l2_note(input_bytes: int) -> str:
+def l2_note(input_bytes: int, l2_bytes: int = L2_BYTES) -> str:
     """How the timed steps stand to the L2 cache (no flush between steps either way)."""
     mb = input_bytes / 1e6
-    if input_bytes > L2_BYTES:
-        return f"inputs larger than L2 ({mb:.0f} MB vs {L2_BYTES >> 20} MiB); no flush"
+    if input_bytes > l2_bytes:
+        return f"inputs larger than L2 ({mb:.0f} MB vs {l2_bytes >> 20} MiB); no flush"
     return (f"inputs ({mb:.2f} MB) fit in L2 and stay resident between steps; no flush "
             "(a latency measurement of one small mesh)")
 
@@ -464,7 +464,9 @@ def run_ours(args, dist: Dist) -> dict | None:
                    "generator": "SplitMix64 16-component Gaussian mixture on a 2^26 lattice, "
                                 "exact Delaunay (seed 2)",
                    "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
-                   "l2": l2_note(16 * n + 24 * m),
+                   "l2": l2_note(16 * n + 24 * m,
+                                 getattr(torch.cuda.get_device_properties(dev), "L2_cache_size",
+                                         L2_BYTES) or L2_BYTES),
                    "step": "polylla_run: label + seeds + traverse + repair, inputs resident"},
         "roofline": roofline,
         # alg_bytes: what the four kernels read and write, each array once (the
